@@ -25,6 +25,8 @@ Algorithm 1.  Writing F_p = sum_l N_l / D_l with N_l = (1/2) sum_ij w_ij
 Reading for p < 2 where |x|^(p-2) is unbounded: the edge term is 0 when
 d_ij == 0 exactly and the vertex term is 0 when u_a == 0 exactly (the paper
 applies no smoothing; a zero difference is treated as a zero-curvature edge).
+At p = 2, |x|^0 = 1 everywhere, so the Hessian of N is exactly 2L (the
+p-Laplacian at p = 2 is the graph Laplacian) even where values tie.
 
 Graphs are any object with integer ``n`` and CSR arrays ``rowptr``, ``col``
 and ``val`` holding both triangles of W.  Blocks U, V are n x k arrays.
@@ -48,8 +50,11 @@ def phi_p(x, p):
 
 
 def abs_pow_pm2(x, p):
-    """|x|^(p-2), read as 0 where x == 0 (the zero-curvature reading)."""
+    """|x|^(p-2); for p < 2 read as 0 where x == 0 (the zero-curvature
+    reading), for p = 2 identically 1."""
     x = np.asarray(x, dtype=np.float64)
+    if p == 2.0:
+        return np.ones_like(x)
     out = np.zeros_like(x)
     nz = x != 0
     out[nz] = np.abs(x[nz]) ** (p - 2.0)

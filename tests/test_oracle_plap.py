@@ -290,3 +290,19 @@ def test_zero_difference_reading(p):
     H = oracle.euclidean_hvp(g, U, V, p)
     assert np.all(np.isfinite(H))
     assert oracle.abs_pow_pm2(np.array([0.0, 2.0]), p)[0] == 0.0
+
+
+def test_p2_hessian_with_ties_is_laplacian():
+    # at p = 2 the sparse part of the Hessian is 2 L / D even where values tie
+    rng = np.random.default_rng(13)
+    n = 16
+    Wd = random_dense_w(rng, n)
+    g = dense_graph(Wd)
+    L = laplacian(Wd)
+    u = np.repeat([0.5, -0.25, 1.0, 0.0], 4)        # ties and zeros
+    eta = rng.standard_normal(n)
+    D = u @ u
+    lam = u @ L @ u / D
+    ref = (2 / D) * (L @ eta - lam * eta) - (4 / D ** 2) * (
+        (L @ u) * (u @ eta) + u * ((L @ u) @ eta) - 2 * lam * u * (u @ eta))
+    assert np.allclose(oracle.euclidean_hvp(g, u, eta, 2.0)[:, 0], ref, rtol=1e-12, atol=1e-13)
