@@ -1,0 +1,391 @@
+"""Benchmark of the p-spectral clustering hot path on GB300.
+
+One step = one pspec_eval (objective + gradient) and one pspec_hvp
+(Hessian-vector product) on the workload's graph: 2 * nnz * k edge-columns.
+The metric is edge-columns per second over the whole job (all ranks), with
+inputs resident in HBM and the L2 flushed (a 256 MB write) before every timed
+step.  Alongside:
+  roofline      the dominant kernel's algorithmic bytes per launch over its
+                mean CUDA-event duration, against the measured HBM copy peak
+  e2e           the same metric through the C ABI with host (pinned) buffers,
+                host<->device copies inside the timed region
+  cpu_baseline  the FP64 oracle on the host cores, on a bounded sample
+  solve         wall time of the full solve down to the schedule's last p,
+                FP32 path vs the plain FP64 path, with their RCut
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload knn_gmm]
+                    [--impl ours|reference] [--no-solve]
+Multi-GPU (torchrun): every rank runs an independent replica (its own seed);
+there is no data-path collective (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2605_26975_gb300 import workloads as wl  # noqa: E402
+
+P_BENCH = 1.3
+L2_FLUSH_BYTES = 256 << 20
+KERNEL_SOURCES = ["paper_2605_26975_gb300/csrc/edge_kernels.cuh",
+                  "paper_2605_26975_gb300/csrc/edge_launch.cuh",
+                  "paper_2605_26975_gb300/csrc/common.cuh"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="knn_gmm", choices=["knn_gmm", "grid3d", "dcsbm", "sbm4"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def describe(name, g, k):
+    desc = {
+        "knn_gmm": "kNN similarity graph: 200,000 points, 8 isotropic 2-D Gaussians, 10-NN symmetrised, w=exp(-d^2/0.25)",
+        "grid3d": "3-D 200^3 6-neighbour grid, w~U[0.5,1.5], 0.1% long-range links",
+        "dcsbm": "degree-corrected SBM, n=1,000,000, 16 blocks, Pareto(2.5) degrees, w~U[0.1,1]",
+        "sbm4": "SBM n=1,000, 4 blocks, p_in 0.05, p_out 0.002",
+    }[name]
+    return f"{desc} (n={g.n}, nnz={g.nnz}, k={k})"
+
+
+def bytes_eval_edges(g, k):
+    return g.nnz * 8 + (g.n + 1) * 8 + 2 * g.n * k * 4
+
+
+def bytes_hvp_edges(g, k):
+    return g.nnz * 8 + (g.n + 1) * 8 + 4 * g.n * k * 4
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic(kernel, workload):
+    """dram bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if "=" in line and not line.startswith("#"):
+            key, _, v = line.partition("=")
+            vals[key.strip()] = v.strip()
+    if vals.get("kernel_source_sha256_16") != source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def build_workload(name, seed_shift=0):
+    info = wl.WORKLOADS[name]
+    if seed_shift == 0:
+        g = wl.make_graph(name)
+        U, V = wl.make_blocks(name, g.n, info["k"])
+    else:  # an independent replica for rank > 0
+        idx = info["index"]
+        g = {"knn_gmm": lambda s: wl.knn_gaussian_mixture(s),
+             "grid3d": lambda s: wl.grid3d_longrange(s),
+             "dcsbm": lambda s: wl.dcsbm_powerlaw(s),
+             "sbm4": lambda s: wl.sbm_bernoulli(s)}[name](1000 + idx + 100 * seed_shift)
+        U = wl.orthonormal_block(2000 + idx + 100 * seed_shift, g.n, info["k"])
+        V = wl.gaussian_block(3000 + idx + 100 * seed_shift, g.n, info["k"])
+    return g, U, V, info
+
+
+def cpu_baseline(g, U, V, p, k, budget_s=12.0):
+    """The oracle as it stands (numpy FP64, one thread) on a bounded sample:
+    full eval+HVP steps on the same graph until ~budget_s seconds pass."""
+    import oracle
+    U64, V64 = U.astype(np.float64), V.astype(np.float64)
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        oracle.objective(g, U64, p)
+        oracle.euclidean_grad(g, U64, p)
+        oracle.euclidean_hvp(g, U64, V64, p)
+        steps += 1
+        if time.perf_counter() - t0 > budget_s or steps >= 20:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": 2 * g.nnz * k * steps / dt, "unit": "edge*col/s", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} full eval+grad+HVP step(s) of the FP64 numpy oracle on this workload "
+                      f"({dt:.1f} s, single-threaded numpy)"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    g, U, V, info = build_workload(args.workload)
+    k = info["k"]
+    # each timed step is one oracle eval+HVP; keep the run to a few minutes
+    import oracle
+    U64, V64 = U.astype(np.float64), V.astype(np.float64)
+    for _ in range(min(args.warmup, 1)):
+        oracle.euclidean_grad(g, U64, P_BENCH)
+    steps = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle.objective(g, U64, P_BENCH)
+        oracle.euclidean_grad(g, U64, P_BENCH)
+        oracle.euclidean_hvp(g, U64, V64, P_BENCH)
+    dt = time.perf_counter() - t0
+    value = 2 * g.nnz * k * steps / dt
+    line = {"impl": "reference", "metric": "p-Laplacian grad+HVP throughput",
+            "value": value, "unit": "edge*col/s", "n_gpus": args.gpus, "steps": steps,
+            "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * dt / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": describe(args.workload, g, k), "p": P_BENCH},
+            "cpu_baseline": {"value": value, "unit": "edge*col/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{steps} eval+grad+HVP step(s) of the FP64 numpy oracle"},
+            "e2e": {"value": value, "unit": "edge*col/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    import torch
+    import torch.distributed as dist
+
+    from paper_2605_26975_gb300 import api, build
+    build.build()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    g, U, V, info = build_workload(args.workload, seed_shift=rank)
+    k = info["k"]
+    G = api.Graph.from_csr(g)
+    Ud = torch.from_numpy(U).cuda()
+    Vd = torch.from_numpy(V).cuda()
+    grad = torch.empty_like(Ud)
+    HV = torch.empty_like(Ud)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        G.eval(Ud, P_BENCH, grad_out=grad)
+        G.hvp(Ud, Vd, P_BENCH, out=HV)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    assert G.status() == 0
+
+    # ---- timed region: device time of every step, L2 flushed before each
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+    edge_cols = 2 * g.nnz * k
+    value = world * edge_cols / (ms * 1e-3)
+
+    # ---- per-kernel device times (same steps, library events on the stream)
+    G.set_timing(True)
+    for _ in range(args.steps):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    times = G.kernel_times()
+    G.set_timing(False)
+    launches = sum(c for c, _ in times.values()) // args.steps
+    shares = {name: t for name, (c, t) in times.items()}
+    dom = max(shares, key=shares.get)
+    dom_launches, dom_ms = times[dom]
+    algo = {"hvp_edges": bytes_hvp_edges(g, k), "eval_edges": bytes_eval_edges(g, k)}.get(dom)
+    peak, peak_kind = measured_peak()
+    roofline = None
+    if algo is not None:
+        achieved = algo / (dom_ms / dom_launches * 1e-3) / 1e9
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
+                    "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                    "traffic": read_traffic(dom, args.workload),
+                    "algorithmic_bytes_per_launch": algo,
+                    "mean_launch_ms": dom_ms / dom_launches,
+                    "kernel_ms_per_step": {n: t / args.steps for n, (c, t) in times.items()}}
+
+    # ---- e2e through the C ABI with pinned host buffers
+    Uh = torch.from_numpy(U).pin_memory()
+    Vh = torch.from_numpy(V).pin_memory()
+    gh = torch.empty_like(Uh).pin_memory()
+    hh = torch.empty_like(Uh).pin_memory()
+    for _ in range(2):
+        G.eval_host(Uh, P_BENCH, gh)
+        G.hvp_host(Uh, Vh, P_BENCH, hh)
+    e2e_steps = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        flush.zero_()
+        G.eval_host(Uh, P_BENCH, gh)
+        G.hvp_host(Uh, Vh, P_BENCH, hh)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    blk = g.n * k * 4
+    e2e = {"value": world * edge_cols / e2e_s, "unit": "edge*col/s",
+           "h2d_bytes_per_step": 3 * blk, "d2h_bytes_per_step": 2 * blk + 8,
+           "note": "wall clock per step incl. a 256 MB L2 flush; copies and kernels synchronous"}
+
+    # ---- full solve to the last p, FP32 fast path vs plain FP64 path
+    solve = None
+    if not args.no_solve and rank == 0:
+        sched = list(info["p_schedule"])
+        opts = api.default_opts()
+        t0 = time.perf_counter()
+        _, lab32, rc32, st32, s32 = G.solve(Ud, sched, opts)
+        t32 = time.perf_counter() - t0
+        U64 = torch.from_numpy(U.astype(np.float64)).cuda()
+        t0 = time.perf_counter()
+        _, lab64, rc64, st64, s64 = G.solve(U64, sched, opts)
+        t64 = time.perf_counter() - t0
+        solve = {"p_schedule": sched, "fast_f32_s": t32, "plain_f64_s": t64,
+                 "speedup": t64 / t32, "rcut_f32": rc32, "rcut_f64": rc64,
+                 "rcut_rel_diff": abs(rc32 - rc64) / rc64,
+                 "hvp_calls_f32": st32["hvp_calls"], "hvp_calls_f64": st64["hvp_calls"],
+                 "newton_steps_f32": sum(st32["outer"]), "newton_steps_f64": sum(st64["outer"])}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(g, U, V, P_BENCH, k)
+
+    if rank == 0:
+        line = {
+            "metric": "p-Laplacian grad+HVP throughput (edge*col/s), % of HBM peak; solve time to p_final vs plain FP64",
+            "value": value, "unit": "edge*col/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": describe(args.workload, g, k), "p": P_BENCH,
+                       "step": "pspec_eval (F + grad) + pspec_hvp",
+                       "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": launches * args.steps, "solve": solve,
+            "wall_s_timed_region": wall,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

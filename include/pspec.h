@@ -1,0 +1,235 @@
+/*
+ * pspec.h -- C ABI of the GB300 (sm_103a) p-spectral clustering library.
+ *
+ * The library evaluates, on one GPU, the hot path of multiway p-spectral
+ * clustering ("Nonlinear spectral clustering with C++ GraphBLAS", Section 2):
+ *
+ *   F_p(U) = sum_l sum_{i,j} w_ij |u_i^l - u_j^l|^p / (2 ||u^l||_p^p)   (Eq. 1)
+ *   (Delta_p u)_i = sum_j w_ij phi_p(u_i - u_j),  phi_p(x) = |x|^(p-1) sign(x)
+ *
+ * its gradient (the paper's EucGrad), the exact Hessian-vector product (the
+ * paper's EucHessianEta, Algorithm 1), the Newton / truncated-CG solve on the
+ * Grassmann manifold with p continuation, the k-means discretisation and the
+ * RCut score (Section 3.1).
+ *
+ * Conventions shared by every call
+ *  - W is symmetric and non-negative, stored in CSR with BOTH triangles:
+ *    rowptr int64[n+1] (rowptr[0] = 0, non-decreasing), col int32[nnz] in
+ *    [0, n), val[nnz].  A stored diagonal entry contributes nothing.
+ *  - Dense blocks (U, V, gradients, Hessian products) are n x k ROW-MAJOR
+ *    (element (i, l) at offset i*k + l; the paper's k x n eta is the
+ *    transpose).  1 <= k <= 16.  FP32 blocks must be 16-byte aligned when
+ *    k % 4 == 0 and 8-byte aligned when k % 2 == 0 (cudaMalloc/torch
+ *    allocations always are); FP64 blocks 8-byte aligned.
+ *  - p lies in (1, 2] (Eq. 1).
+ *  - Precision (pspec_dtype): PSPEC_F32 is the fast form (FP32 edge
+ *    arithmetic, compensated FP32 per-thread sums, float-float cross-thread
+ *    reductions, FP64 scalars); PSPEC_F64 is the plain form (FP64 everywhere,
+ *    one thread per row, one column per pass, mirroring Algorithm 1's loop
+ *    over columns).
+ *  - Pointers are DEVICE pointers unless the call's flags contain
+ *    PSPEC_HOST_PTRS.  The caller owns every pointer it passes; the graph
+ *    handle owns its device copy of W and its workspace.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are stream ordered and return once the work is
+ *    enqueued, except: calls with PSPEC_HOST_PTRS, pspec_solve,
+ *    pspec_kmeans and pspec_rcut, which synchronise `stream` before they
+ *    return.
+ *  - Errors are returned as pspec_status; no C++ exception crosses the ABI.
+ *    pspec_last_error() gives a message for the calling thread's last error.
+ *    Conditions found by a kernel (a zero column norm, a non-finite result)
+ *    are recorded in the graph's device status word: synchronous calls
+ *    return them, asynchronous ones leave them for pspec_graph_status().
+ *  - A graph handle may be used from one host thread at a time; calls on the
+ *    same handle must be ordered on one stream (they share its workspace).
+ */
+#ifndef PSPEC_H
+#define PSPEC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PSPEC_OK = 0,
+  PSPEC_ERR_INVALID_ARG = 1,   /* argument outside its documented domain   */
+  PSPEC_ERR_CUDA = 2,          /* a CUDA runtime call failed               */
+  PSPEC_ERR_OOM = 3,           /* device or pinned-host allocation failed  */
+  PSPEC_ERR_ZERO_COLUMN = 4,   /* ||u^l||_p = 0 for some column            */
+  PSPEC_ERR_NONFINITE = 5,     /* a NaN or Inf reached an objective sum    */
+  PSPEC_ERR_NOT_CONVERGED = 6, /* iteration cap reached (informational)    */
+  PSPEC_ERR_TIMEOUT = 7        /* a bounded device wait gave up            */
+} pspec_status;
+
+typedef enum { PSPEC_F32 = 0, PSPEC_F64 = 1 } pspec_dtype;
+
+/* flags */
+#define PSPEC_HOST_PTRS 0x1u      /* pointer arguments are host memory         */
+#define PSPEC_CHECK_SYMMETRY 0x2u /* graph_create: verify w_ij == w_ji (host)  */
+
+typedef struct pspec_graph pspec_graph;
+
+/* ---------------------------------------------------------------- graph ---
+ * pspec_graph_create: copy W (CSR, both triangles; Section 2's weighted
+ * adjacency of an undirected graph) to the device and build the row
+ * partition the edge kernels walk.  rowptr/col/val are host pointers (or
+ * device pointers without PSPEC_HOST_PTRS: they are then staged through the
+ * host).  val_dtype gives val's type; the graph keeps an FP32 and an FP64
+ * copy so either precision can run on it.
+ * Errors: INVALID_ARG for n < 1, nnz >= 2^31, rowptr[0] != 0, a decreasing
+ * rowptr, col outside [0, n), a negative or non-finite weight, or (with
+ * PSPEC_CHECK_SYMMETRY) an entry without its mirror of equal weight; OOM;
+ * CUDA.  On error *out is set to NULL. */
+pspec_status pspec_graph_create(int64_t n, const int64_t* rowptr, const int32_t* col,
+                                const void* val, pspec_dtype val_dtype, unsigned flags,
+                                void* stream, pspec_graph** out);
+
+/* pspec_graph_create_batched: G independent graphs concatenated into one
+ * block-diagonal W.  node_off int64[G+1] (node_off[0] = 0) gives each
+ * graph's vertex range; rowptr/col/val describe the concatenation with GLOBAL
+ * column indices that must stay inside the row's own graph.  Batched eval
+ * and HVP calls then treat every graph as its own problem (its own F, N_l,
+ * D_l) in one launch.  Same errors as pspec_graph_create, plus INVALID_ARG
+ * when an entry crosses graphs. */
+pspec_status pspec_graph_create_batched(int32_t n_graphs, const int64_t* node_off,
+                                        const int64_t* rowptr, const int32_t* col,
+                                        const void* val, pspec_dtype val_dtype, unsigned flags,
+                                        void* stream, pspec_graph** out);
+
+/* Free the device copy and workspace.  NULL is accepted. */
+void pspec_graph_destroy(pspec_graph* g);
+
+/* n (vertices), nnz (stored entries), graph count of a handle. */
+pspec_status pspec_graph_info(const pspec_graph* g, int64_t* n, int64_t* nnz, int32_t* n_graphs);
+
+/* Synchronise `stream`, return the conditions kernels recorded since the
+ * last call (ZERO_COLUMN, NONFINITE, TIMEOUT, or OK) and clear them. */
+pspec_status pspec_graph_status(pspec_graph* g, void* stream);
+
+/* ----------------------------------------------------------------- eval ---
+ * pspec_eval: objective and Euclidean gradient (the paper's EucGrad).
+ *   F_out[0]   = F_p(U) of Eq. 1                          (FP64, 1 value)
+ *   grad_out   = dF/dU, column l = (p/D_l)(Delta_p u^l - lambda_l phi_p(u^l))
+ *                with D_l = ||u^l||_p^p, N_l = (1/2) sum_ij w_ij |d_ij|^p,
+ *                lambda_l = N_l / D_l                     (n x k, dtype)
+ *   parts_out  = optional (NULL to skip) FP64[2k]: N_0..N_{k-1}, D_0..D_{k-1}
+ * U and grad_out have type `dtype`; grad_out may not alias U.  F_out and
+ * parts_out are device pointers (host with PSPEC_HOST_PTRS).  On a batched
+ * graph F_out and parts_out hold one entry per graph (F_out[G],
+ * parts_out[G][2k]) and k is the row stride shared by all graphs.
+ * Errors: INVALID_ARG (k, p, NULL, misalignment), CUDA; ZERO_COLUMN and
+ * NONFINITE through the status word. */
+pspec_status pspec_eval(pspec_graph* g, const void* U, int k, double p, pspec_dtype dtype,
+                        double* F_out, void* grad_out, double* parts_out, unsigned flags,
+                        void* stream);
+
+/* ------------------------------------------------------------------ hvp ---
+ * pspec_hvp: exact Euclidean Hessian of F_p at U applied to V (the paper's
+ * EucHessianEta; block diagonal over columns):
+ *   HV = (Hess N V - lambda Hess D V)/D
+ *        - (g_N <g_D,V> + g_D <g_N,V> - 2 lambda g_D <g_D,V>)/D^2   per column,
+ *   (Hess N V)_a = p(p-1) sum_j w_aj |d_aj|^(p-2) (V_a - V_j),
+ *   (Hess D V)_a = p(p-1) |u_a|^(p-2) V_a,  g_N = p Delta_p u,  g_D = p phi_p(u).
+ * A zero difference d_aj == 0 (or u_a == 0) contributes no curvature term.
+ * The sparse-plus-diagonal part is what Algorithm 1 applies column by
+ * column; the rank-two terms complete the Hessian of the quotient.
+ * HV_out may not alias U or V.  Errors as pspec_eval. */
+pspec_status pspec_hvp(pspec_graph* g, const void* U, const void* V, int k, double p,
+                       pspec_dtype dtype, void* HV_out, unsigned flags, void* stream);
+
+/* ---------------------------------------------------------------- solve ---
+ * pspec_solve: minimise Eq. 1 "for progressively smaller values of p"
+ * (Section 2): for each p of p_schedule (each in (1,2], non-increasing), a
+ * trust-region Newton method on Gr(k, n) whose subproblems are solved by
+ * truncated CG; tangent projection P_U(G) = G - U U^T G, Riemannian Hessian
+ * P_U(H eta) - eta U^T grad F, retraction qf(U + eta) (thin QR with a
+ * positive diagonal, computed as Cholesky-QR twice).  Then k-means on the
+ * rows of U (k clusters, opts' seed/restarts) and the RCut of the labels.
+ *   U_inout   device n x k (dtype): U0 in (orthonormal columns expected),
+ *             final U out
+ *   labels_out device int32[n] (may be NULL), rcut_out host double (may be
+ *             NULL), stats host (may be NULL).
+ * Synchronises `stream`.  Returns OK, or NOT_CONVERGED when a stage hit
+ * max_outer (the result is still written).  Not for batched graphs. */
+typedef struct {
+  int32_t max_outer;       /* Newton steps per p (default 30)                 */
+  int32_t max_inner;       /* truncated-CG steps per Newton step (50)         */
+  double gtol_rel;         /* stop: ||grad|| <= gtol_rel ||grad_stage0|| (1e-6) */
+  double gtol_abs;         /* ... or ||grad|| <= gtol_abs (0)                  */
+  double theta;            /* tCG exponent (1.0)                               */
+  double kappa;            /* tCG linear factor (0.1)                          */
+  double delta_bar_scale;  /* Delta_bar = scale * sqrt(k) (1.0)                */
+  double delta0_scale;     /* Delta_0 = scale * Delta_bar (0.1)                */
+  double rho_prime;        /* acceptance threshold (0.1)                       */
+  double rho_reg;          /* ratio regularisation, times max(1,|f|) (1e-10)   */
+  int32_t kmeans_restarts; /* (10)                                             */
+  int32_t kmeans_max_iter; /* (300)                                            */
+  uint64_t seed;           /* k-means seed (0)                                 */
+  int32_t verbose;         /* print one line per Newton step to stderr (0)     */
+} pspec_solve_opts;
+
+typedef struct {
+  int32_t n_stages;
+  int32_t outer[32];       /* Newton steps per stage (first 32 stages)        */
+  int32_t inner[32];       /* truncated-CG steps per stage                    */
+  double f[32];            /* F_p at the end of each stage                    */
+  double gnorm[32];        /* ||Riemannian gradient|| at the end              */
+  int64_t hvp_calls;       /* total Hessian-vector products                   */
+  int64_t eval_calls;      /* total objective/gradient evaluations            */
+  double seconds;          /* wall time of the solve (host clock)             */
+  double kmeans_inertia;
+} pspec_solve_stats;
+
+void pspec_solve_opts_default(pspec_solve_opts* o);
+
+pspec_status pspec_solve(pspec_graph* g, int k, const double* p_schedule, int n_p,
+                         const pspec_solve_opts* opts, pspec_dtype dtype, void* U_inout,
+                         int32_t* labels_out, double* rcut_out, pspec_solve_stats* stats,
+                         void* stream);
+
+/* --------------------------------------------------------------- kmeans ---
+ * pspec_kmeans: k-means of the n rows of X (n x dim, row-major, dtype,
+ * device), the discretisation step of Section 1/2.  k-means++ seeding whose
+ * uniforms come from SplitMix64(seed) (x >> 11) * 2^-53, consumed in order
+ * across restarts; Lloyd iterations with squared distances accumulated in
+ * FP64 dimension by dimension; ties to the smallest centre; an empty
+ * cluster is re-seeded at the row farthest from its centre; stop when no
+ * label changes or after max_iter updates; the restart with the smallest
+ * inertia is kept.  1 <= dim <= 16, 1 <= n_clusters <= 64, n >= n_clusters.
+ *   labels_out device int32[n]; centers_out device FP64[n_clusters*dim]
+ *   (may be NULL); inertia_out host double (may be NULL).
+ * Synchronises `stream`. */
+pspec_status pspec_kmeans(const void* X, int64_t n, int dim, pspec_dtype dtype, int n_clusters,
+                          uint64_t seed, int restarts, int max_iter, int32_t* labels_out,
+                          double* centers_out, double* inertia_out, void* stream);
+
+/* ----------------------------------------------------------------- rcut ---
+ * pspec_rcut: RCut(C_1..C_c) = sum_c cut(C_c, complement)/|C_c| (Section
+ * 3.1) with cut(C, C') = sum over i in C, j in C' of w_ij; empty clusters
+ * contribute nothing.  labels device int32[n] in [0, n_clusters).
+ * rcut_out host double.  Synchronises `stream`. */
+pspec_status pspec_rcut(pspec_graph* g, const int32_t* labels, int n_clusters, double* rcut_out,
+                        void* stream);
+
+/* ------------------------------------------------------- instrumentation ---
+ * Per-kernel timing: while enabled, every kernel the graph launches is
+ * bracketed by CUDA events on its stream; pspec_kernel_times returns, per
+ * kernel name, the number of launches and the summed device milliseconds
+ * (it synchronises the recorded events).  Names are returned in a
+ * caller-provided buffer as "name=launches:ms;..." */
+pspec_status pspec_set_timing(pspec_graph* g, int enable);
+pspec_status pspec_kernel_times(pspec_graph* g, char* buf, size_t buf_len);
+
+/* Thread-local message of the last error on this thread ("" if none). */
+const char* pspec_last_error(void);
+
+/* Library version "major.minor.patch" and the arch it was built for. */
+const char* pspec_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSPEC_H */

@@ -1,0 +1,201 @@
+"""Python binding of the C ABI on torch tensors (marshalling only).
+
+Every computation runs in libpspec.so's CUDA kernels; this module only checks
+tensor placement and dtypes, passes data pointers and the current CUDA
+stream, and raises PspecError on a non-OK status.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import check, lib
+
+_DT = {torch.float32: _abi.PSPEC_F32, torch.float64: _abi.PSPEC_F64}
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _dev_block(t, name, n=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype not in _DT:
+        raise TypeError(f"{name} must be float32 or float64")
+    if t.dim() != 2 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous n x k tensor")
+    if n is not None and t.shape[0] != n:
+        raise ValueError(f"{name} has {t.shape[0]} rows, the graph has {n}")
+    return t
+
+
+class Graph:
+    """A symmetric weight matrix W on the device (pspec_graph_create)."""
+
+    def __init__(self, rowptr, col, val, check_symmetry=False, node_off=None):
+        rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        val = np.ascontiguousarray(val)
+        if val.dtype not in (np.float32, np.float64):
+            val = val.astype(np.float64)
+        vt = _abi.PSPEC_F32 if val.dtype == np.float32 else _abi.PSPEC_F64
+        flags = _abi.PSPEC_HOST_PTRS | (_abi.PSPEC_CHECK_SYMMETRY if check_symmetry else 0)
+        h = C.c_void_p()
+        if node_off is None:
+            st = lib().pspec_graph_create(rowptr.size - 1, rowptr.ctypes.data, col.ctypes.data,
+                                          val.ctypes.data, vt, flags, _stream(), C.byref(h))
+            check(st, "pspec_graph_create")
+        else:
+            node_off = np.ascontiguousarray(node_off, dtype=np.int64)
+            st = lib().pspec_graph_create_batched(node_off.size - 1, node_off.ctypes.data,
+                                                  rowptr.ctypes.data, col.ctypes.data,
+                                                  val.ctypes.data, vt, flags, _stream(), C.byref(h))
+            check(st, "pspec_graph_create_batched")
+        self._h = h
+        n, nnz, ng = C.c_int64(), C.c_int64(), C.c_int32()
+        check(lib().pspec_graph_info(h, C.byref(n), C.byref(nnz), C.byref(ng)), "pspec_graph_info")
+        self.n, self.nnz, self.n_graphs = n.value, nnz.value, ng.value
+
+    @classmethod
+    def from_csr(cls, g, **kw):
+        return cls(g.rowptr, g.col, g.val, **kw)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().pspec_graph_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ per call
+    def eval(self, U, p, grad_out=None, parts=False):
+        """(F, grad[, parts]) with F a 1-element float64 CUDA tensor."""
+        U = _dev_block(U, "U", self.n)
+        k = U.shape[1]
+        grad = torch.empty_like(U) if grad_out is None else grad_out
+        F = torch.empty(1, dtype=torch.float64, device=U.device)
+        P = torch.empty(2 * k, dtype=torch.float64, device=U.device) if parts else None
+        st = lib().pspec_eval(self._h, _ptr(U), k, float(p), _DT[U.dtype], _ptr(F), _ptr(grad),
+                              _ptr(P), 0, _stream())
+        check(st, "pspec_eval")
+        return (F, grad, P) if parts else (F, grad)
+
+    def hvp(self, U, V, p, out=None):
+        U = _dev_block(U, "U", self.n)
+        V = _dev_block(V, "V", self.n)
+        if V.shape != U.shape or V.dtype != U.dtype:
+            raise ValueError("U and V must have the same shape and dtype")
+        HV = torch.empty_like(U) if out is None else out
+        st = lib().pspec_hvp(self._h, _ptr(U), _ptr(V), U.shape[1], float(p), _DT[U.dtype],
+                             _ptr(HV), 0, _stream())
+        check(st, "pspec_hvp")
+        return HV
+
+    def eval_host(self, U, p, grad_out):
+        """pspec_eval with PSPEC_HOST_PTRS: U and grad_out are CPU tensors
+        (pinned for asynchronous copies); returns F as a Python float."""
+        k = U.shape[1]
+        F = C.c_double()
+        st = lib().pspec_eval(self._h, C.c_void_p(U.data_ptr()), k, float(p), _DT[U.dtype],
+                              C.byref(F), C.c_void_p(grad_out.data_ptr()), None,
+                              _abi.PSPEC_HOST_PTRS, _stream())
+        check(st, "pspec_eval(host)")
+        return F.value
+
+    def hvp_host(self, U, V, p, out):
+        st = lib().pspec_hvp(self._h, C.c_void_p(U.data_ptr()), C.c_void_p(V.data_ptr()),
+                             U.shape[1], float(p), _DT[U.dtype], C.c_void_p(out.data_ptr()),
+                             _abi.PSPEC_HOST_PTRS, _stream())
+        check(st, "pspec_hvp(host)")
+        return out
+
+    def status(self):
+        """Synchronise and return (and clear) the kernel-recorded status."""
+        return lib().pspec_graph_status(self._h, _stream())
+
+    # --------------------------------------------------------------- solve
+    def solve(self, U0, p_schedule, opts=None, labels=True):
+        """Trust-region Newton + tCG over the p schedule, k-means, RCut.
+        Returns (U, labels, rcut, stats dict, status)."""
+        U = _dev_block(U0, "U0", self.n).clone()
+        k = U.shape[1]
+        o = default_opts() if opts is None else opts
+        sched = np.ascontiguousarray(p_schedule, dtype=np.float64)
+        lab = torch.empty(self.n, dtype=torch.int32, device=U.device) if labels else None
+        rc = C.c_double(float("nan"))
+        stats = _abi.SolveStats()
+        st = lib().pspec_solve(self._h, k, sched.ctypes.data, sched.size, C.byref(o), _DT[U.dtype],
+                               _ptr(U), _ptr(lab), C.byref(rc), C.byref(stats), _stream())
+        check(st, "pspec_solve", allow=(_abi.PSPEC_OK, _abi.PSPEC_ERR_NOT_CONVERGED))
+        ns = stats.n_stages
+        sd = dict(outer=list(stats.outer[:ns]), inner=list(stats.inner[:ns]), f=list(stats.f[:ns]),
+                  gnorm=list(stats.gnorm[:ns]), hvp_calls=stats.hvp_calls,
+                  eval_calls=stats.eval_calls, seconds=stats.seconds,
+                  kmeans_inertia=stats.kmeans_inertia)
+        return U, lab, rc.value, sd, st
+
+    def rcut(self, labels, n_clusters):
+        if not labels.is_cuda or labels.dtype != torch.int32:
+            raise TypeError("labels must be an int32 CUDA tensor")
+        out = C.c_double()
+        check(lib().pspec_rcut(self._h, _ptr(labels), int(n_clusters), C.byref(out), _stream()),
+              "pspec_rcut")
+        return out.value
+
+    # --------------------------------------------------------- timing
+    def set_timing(self, enable=True):
+        check(lib().pspec_set_timing(self._h, 1 if enable else 0), "pspec_set_timing")
+
+    def kernel_times(self):
+        """{kernel name: (launches, total ms)} since the last call."""
+        buf = C.create_string_buffer(8192)
+        check(lib().pspec_kernel_times(self._h, buf, len(buf)), "pspec_kernel_times")
+        out = {}
+        for item in buf.value.decode().split(";"):
+            if item:
+                name, rest = item.split("=")
+                cnt, ms = rest.split(":")
+                out[name] = (int(cnt), float(ms))
+        return out
+
+
+def default_opts(**kw):
+    o = _abi.SolveOpts()
+    lib().pspec_solve_opts_default(C.byref(o))
+    for key, v in kw.items():
+        setattr(o, key, v)
+    return o
+
+
+def kmeans(X, n_clusters, seed=0, restarts=10, max_iter=300):
+    """k-means of the rows of X (CUDA tensor); returns (labels, centers, inertia)."""
+    X = _dev_block(X, "X")
+    n, dim = X.shape
+    labels = torch.empty(n, dtype=torch.int32, device=X.device)
+    centers = torch.empty((n_clusters, dim), dtype=torch.float64, device=X.device)
+    inertia = C.c_double()
+    st = lib().pspec_kmeans(_ptr(X), n, dim, _DT[X.dtype], int(n_clusters), C.c_uint64(seed),
+                            int(restarts), int(max_iter), _ptr(labels), _ptr(centers),
+                            C.byref(inertia), _stream())
+    check(st, "pspec_kmeans")
+    return labels, centers, inertia.value
+
+
+def version():
+    return lib().pspec_version().decode()

@@ -1,0 +1,60 @@
+// Host launcher of the fused edge kernels for one column count K; explicit
+// instantiations live in edge_k*.cu so the 32 kernels compile in parallel.
+#pragma once
+
+#include <algorithm>
+
+#include "edge_kernels.cuh"
+#include "internal.h"
+
+namespace pspec {
+
+template <int K, bool HVP>
+pspec_status launch_edges_k(pspec_graph* g, const EdgeLaunch& L, cudaStream_t s) {
+  constexpr int Q = q_of(K);
+  PSPEC_TRY(ensure_tasks(g, Q));
+  const TaskSet& ts = g->tasks[Q == 1 ? 0 : Q == 2 ? 1 : 2];
+  static int occ = -1;
+  if (occ < 0) {
+    PSPEC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, edge_kernel<K, HVP>, kBlock, 0));
+    occ = std::max(occ, 1);
+  }
+  EdgeArgs a;
+  a.rowptr = g->d_rowptr;
+  a.col = g->d_col;
+  a.val = g->d_val32;
+  a.U = L.U;
+  a.V = L.V;
+  a.out_a = L.out_a;
+  a.out_b = L.out_b;
+  a.tasks = ts.d_tasks;
+  a.n_tasks = (int)ts.n_tasks;
+  a.chunk_edges = ts.chunk_edges;
+  a.hub_part = g->d_hub_part;
+  a.hub_first = ts.d_hub_first;
+  a.hub_nchunk = ts.d_hub_nchunk;
+  a.chunk_hub = ts.d_chunk_hub;
+  a.hub_ticket = ts.d_hub_ticket;
+  a.p = L.p;
+  a.pm2 = L.p - 2.0f;
+  a.gr.block_part = g->d_block_part;
+  a.gr.group_part = g->d_group_part;
+  a.gr.counters = g->d_counters;
+  a.scalars = g->d_scalars;
+  a.status = g->d_status;
+  a.skip = L.skip;
+  int blocks = grid_blocks(g, occ);
+  blocks = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (ts.n_tasks + kWarps - 1) / kWarps));
+  TimedScope timer(g, HVP ? "hvp_edges" : "eval_edges", s);
+  edge_kernel<K, HVP><<<blocks, kBlock, 0, s>>>(a);
+  PSPEC_CUDA(cudaGetLastError());
+  return PSPEC_OK;
+}
+
+}  // namespace pspec
+
+#define PSPEC_INSTANTIATE_EDGES(K)                                                          \
+  template pspec_status pspec::launch_edges_k<K, false>(pspec_graph*, const pspec::EdgeLaunch&, \
+                                                        cudaStream_t);                      \
+  template pspec_status pspec::launch_edges_k<K, true>(pspec_graph*, const pspec::EdgeLaunch&,  \
+                                                       cudaStream_t);

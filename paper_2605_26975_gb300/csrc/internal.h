@@ -1,0 +1,163 @@
+// Host-side internals of the p-spectral clustering library: the graph handle,
+// its device workspace, error plumbing and per-kernel timing.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "pspec.h"
+
+namespace pspec {
+
+// ------------------------------------------------------------ row tasks ---
+// The edge kernels walk a list of warp tasks.  A plain task covers `nrows`
+// consecutive rows starting at `row`, each row processed by a team of
+// E = 2^elog edge slots x Q column lanes (E*Q*nrows <= 32).  A hub chunk task
+// covers edges [rowptr[row] + chunk*chunk_edges, ...) of one long row with the
+// whole warp; its partial row sums go to hub slot `slot`, and the warp that
+// finishes the row's last chunk adds the chunks up in chunk order.
+struct TaskSet {
+  bool built = false;
+  int Q = 0;
+  int chunk_edges = 0;
+  int64_t n_tasks = 0;
+  int n_hubs = 0;
+  int n_chunks = 0;
+  int4* d_tasks = nullptr;          // x=row, y=nrows|chunk, z=elog|(hub<<8), w=slot
+  int32_t* d_hub_row = nullptr;     // [n_hubs]
+  int32_t* d_hub_first = nullptr;   // [n_hubs] first slot of the hub's chunks
+  int32_t* d_hub_nchunk = nullptr;  // [n_hubs]
+  unsigned* d_hub_ticket = nullptr; // [n_hubs] chunk completion counters
+  int32_t* d_chunk_hub = nullptr;   // [n_chunks] hub index of each chunk
+};
+
+struct Timing {
+  bool enabled = false;
+  struct Pending {
+    std::string name;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  std::map<std::string, std::pair<long long, double>> totals;
+};
+
+}  // namespace pspec
+
+struct pspec_graph {
+  int64_t n = 0, nnz = 0;
+  int32_t n_graphs = 1;
+  int device = 0;
+  int sm_count = 0;
+  // device CSR
+  int64_t* d_rowptr = nullptr;
+  int32_t* d_col = nullptr;
+  float* d_val32 = nullptr;
+  double* d_val64 = nullptr;
+  std::vector<int64_t> h_rowptr;     // host copy (task building, batching)
+  // batched graphs
+  std::vector<int64_t> h_node_off;
+  int64_t* d_node_off = nullptr;
+  // edge-kernel partitions, one per column split Q in {1, 2, 4}
+  pspec::TaskSet tasks[3];
+  // workspace
+  float* d_scratch = nullptr;        // n x 16 floats (HVP's Delta rows)
+  size_t scratch_elems = 0;
+  float* d_hub_part = nullptr;       // [max chunks][2*16] partial row sums
+  size_t hub_part_elems = 0;
+  float2* d_block_part = nullptr;    // [max blocks][64]
+  float2* d_group_part = nullptr;    // [max groups][64]
+  unsigned* d_counters = nullptr;    // [max groups + 1]
+  double* d_scalars = nullptr;       // [512] per-call FP64 scalars
+  double* d_red64 = nullptr;         // FP64 block partials of the plain path
+  int* d_status = nullptr;           // kernel-recorded conditions
+  int max_blocks = 0;
+  // host staging for PSPEC_HOST_PTRS calls
+  void* h_pinned = nullptr;
+  size_t h_pinned_bytes = 0;
+  void* d_io = nullptr;
+  size_t d_io_bytes = 0;
+  // solver workspace (allocated on first solve)
+  void* d_solve = nullptr;
+  size_t d_solve_bytes = 0;
+  pspec::Timing timing;
+};
+
+namespace pspec {
+
+// error plumbing -----------------------------------------------------------
+pspec_status set_error(pspec_status s, const std::string& msg);
+pspec_status cuda_error(cudaError_t e, const char* what);
+#define PSPEC_CUDA(call)                                   \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return ::pspec::cuda_error(e_, #call); \
+  } while (0)
+#define PSPEC_TRY(call)                    \
+  do {                                     \
+    pspec_status s_ = (call);              \
+    if (s_ != PSPEC_OK) return s_;         \
+  } while (0)
+
+// timing: wrap a launch
+void timing_begin(pspec_graph* g, const char* name, cudaStream_t s, int* slot);
+void timing_end(pspec_graph* g, int slot, cudaStream_t s);
+
+struct TimedScope {
+  pspec_graph* g;
+  cudaStream_t s;
+  int slot = -1;
+  TimedScope(pspec_graph* g_, const char* name, cudaStream_t s_) : g(g_), s(s_) {
+    if (g && g->timing.enabled) timing_begin(g, name, s, &slot);
+  }
+  ~TimedScope() {
+    if (slot >= 0) timing_end(g, slot, s);
+  }
+};
+
+// task sets and workspace
+pspec_status ensure_tasks(pspec_graph* g, int Q);
+pspec_status ensure_io(pspec_graph* g, size_t bytes);
+int grid_blocks(pspec_graph* g, int blocks_per_sm);
+pspec_status check_block(const void* ptr, int k, pspec_dtype dtype, const char* name);
+pspec_status check_common(pspec_graph* g, int k, double p);
+pspec_status take_status(pspec_graph* g, cudaStream_t s);
+
+// launchers (FP32 fast path), implemented per k in edge_*.cu
+struct EdgeLaunch {
+  const float* U;
+  const float* V;      // HVP only
+  float* out_a;        // eval: Delta; HVP: sparse part S
+  float* out_b;        // HVP: Delta
+  float p;
+  int k;
+  const int* skip = nullptr;  // device flag: when nonzero the launch does nothing
+};
+pspec_status launch_eval_edges(pspec_graph* g, const EdgeLaunch& a, cudaStream_t s);
+pspec_status launch_hvp_edges(pspec_graph* g, const EdgeLaunch& a, cudaStream_t s);
+
+// FP64 plain path
+pspec_status eval_plain64(pspec_graph* g, const double* U, int k, double p, double* F_out,
+                          double* grad, double* parts, cudaStream_t s);
+pspec_status hvp_plain64(pspec_graph* g, const double* U, const double* V, int k, double p,
+                         double* HV, cudaStream_t s);
+
+// FP32 fast path, device pointers only
+pspec_status eval_fast(pspec_graph* g, const float* U, int k, double p, double* F_out,
+                       float* grad, double* parts, cudaStream_t s);
+pspec_status hvp_fast(pspec_graph* g, const float* U, const float* V, int k, double p, float* HV,
+                      cudaStream_t s, const int* skip = nullptr);
+
+// scalar slots in d_scalars
+constexpr int kSlotN = 0;      // [16]
+constexpr int kSlotD = 16;     // [16]
+constexpr int kSlotCN = 32;    // [16] sum_i Delta_i V_i
+constexpr int kSlotCD = 48;    // [16] sum_i phi_p(u_i) V_i
+constexpr int kSlotF = 64;     // [1]
+constexpr int kSlotCoef = 80;  // [6*16] epilogue coefficients
+
+}  // namespace pspec

@@ -1,0 +1,362 @@
+// pspec_solve: the paper's solve (Section 2) -- F_p minimised on the
+// Grassmann manifold by Newton's method with truncated-CG subproblems, "for
+// progressively smaller values of p" -- followed by k-means and RCut.
+//
+// Reading taken (the paper delegates these to ROPTLIB and prints no detail;
+// the CPU oracle follows the same reading): the Riemannian trust-region
+// Newton method of Absil, Baker & Gallivan with Steihaug-Toint truncated CG
+// (no preconditioner, recurrences for <eta,delta> and <delta,delta>), the
+// tangent projection P_U(G) = G - U U^T G, the Riemannian Hessian
+// P_U(H eta) - eta U^T grad F, the retraction qf(U + eta) computed as
+// Cholesky-QR twice, the radius update with the 1/4 and 3/4 rules, acceptance
+// when the model decreased and rho > rho_prime, and rho regularised by
+// rho_reg * max(1, |f|).
+//
+// Device / host split: every n x k operation is a kernel; the CG scalar
+// recurrences run in the last block of the reduction kernels, so truncated CG
+// proceeds on the device in chunks of iterations and the host reads one small
+// state record per chunk (the kernels of iterations enqueued after CG stopped
+// return immediately).  The host does the per-Newton-step trust-region
+// arithmetic on a handful of FP64 scalars.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "internal.h"
+#include "solve_kernels.cuh"
+
+namespace pspec {
+
+namespace {
+
+template <typename T>
+struct SolveWork {
+  T *U, *Unew, *egrad, *egrad_new, *rg, *eta, *Heta, *r, *delta, *He, *Hd, *tmp;
+  double *M, *G, *Gram, *Rinv, *dots, *F;
+  TcgState* st;
+  int* bad;
+  GridRed gr;
+  int vblocks, gblocks;
+};
+
+template <typename T>
+pspec_status carve(pspec_graph* g, int k, SolveWork<T>* w) {
+  const size_t m = (size_t)g->n * k;
+  const size_t vec = ((sizeof(T) * m + 255) / 256) * 256;
+  w->vblocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * 4, ((int64_t)m + kSolveBlock - 1) / kSolveBlock));
+  w->gblocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * 2, (g->n + 7) / 8));
+  const int maxb = std::max(w->vblocks, w->gblocks);
+  const int groups = (maxb + kGroup - 1) / kGroup;
+  const size_t red = sizeof(double) * 256 * (size_t)(maxb + groups);
+  const size_t small = 4096 * sizeof(double);
+  const size_t need = 12 * vec + 2 * red + small;
+  if (g->d_solve_bytes < need) {
+    if (g->d_solve) cudaFree(g->d_solve);
+    g->d_solve = nullptr;
+    g->d_solve_bytes = 0;
+    PSPEC_CUDA(cudaMalloc(&g->d_solve, need));
+    g->d_solve_bytes = need;
+  }
+  char* p = (char*)g->d_solve;
+  T** vecs[12] = {&w->U, &w->Unew, &w->egrad, &w->egrad_new, &w->rg, &w->eta,
+                  &w->Heta, &w->r, &w->delta, &w->He, &w->Hd, &w->tmp};
+  for (auto v : vecs) {
+    *v = (T*)p;
+    p += vec;
+  }
+  w->gr.block_part = p;
+  w->gr.group_part = p + sizeof(double) * 256 * (size_t)maxb;
+  p += 2 * red;
+  double* sm = (double*)p;
+  w->M = sm;
+  w->G = sm + 256;
+  w->Gram = sm + 512;
+  w->Rinv = sm + 768;
+  w->dots = sm + 1024;
+  w->F = sm + 1040;
+  w->st = (TcgState*)(sm + 1056);
+  w->bad = (int*)(sm + 1100);
+  w->gr.counters = g->d_counters;
+  return PSPEC_OK;
+}
+
+template <typename T>
+struct Solver {
+  pspec_graph* g;
+  int k;
+  int64_t n, m;
+  cudaStream_t s;
+  SolveWork<T> w;
+  int64_t evals = 0, hvps = 0;
+
+  pspec_status eval(const T* U, double p, T* grad) {
+    ++evals;
+    if constexpr (sizeof(T) == 4)
+      return eval_fast(g, U, k, p, w.F, grad, nullptr, s);
+    else
+      return eval_plain64(g, U, k, p, w.F, grad, nullptr, s);
+  }
+  pspec_status hvp(const T* U, const T* V, double p, T* out, const int* skip) {
+    if constexpr (sizeof(T) == 4)
+      return hvp_fast(g, U, V, k, p, out, s, skip);
+    else
+      return hvp_plain64(g, U, V, k, p, out, s);
+  }
+  pspec_status gram(const T* A, const T* B, double* G, const int* done = nullptr) {
+    TimedScope timer(g, "solve_gram", s);
+    gram_kernel<T><<<w.gblocks, kSolveBlock, 0, s>>>(A, B, n, k, G, w.gr, done);
+    PSPEC_CUDA(cudaGetLastError());
+    return PSPEC_OK;
+  }
+  pspec_status dots(DotPairs<T> dp, double* out) {
+    TimedScope timer(g, "solve_dots", s);
+    dots_kernel<T><<<w.vblocks, kSolveBlock, 0, s>>>(dp, m, out, w.gr, nullptr);
+    PSPEC_CUDA(cudaGetLastError());
+    return PSPEC_OK;
+  }
+  pspec_status combine(T* out, const T* X, double a, const T* Y, double b, const T* P,
+                       const double* M1, const T* Q, const double* M2) {
+    TimedScope timer(g, "solve_combine", s);
+    combine_kernel<T><<<w.vblocks, kSolveBlock, 0, s>>>(out, X, a, Y, b, P, M1, Q, M2, n, k, nullptr);
+    PSPEC_CUDA(cudaGetLastError());
+    return PSPEC_OK;
+  }
+  // out = qf(A) by Cholesky-QR twice; A is overwritten
+  pspec_status qf(T* A, T* out) {
+    PSPEC_TRY(gram(A, A, w.Gram));
+    chol_inv_kernel<<<1, 1, 0, s>>>(w.Gram, k, w.Rinv, w.bad);
+    rmul_kernel<T><<<w.vblocks, kSolveBlock, 0, s>>>(out, A, w.Rinv, n, k);
+    PSPEC_TRY(gram(out, out, w.Gram));
+    chol_inv_kernel<<<1, 1, 0, s>>>(w.Gram, k, w.Rinv, w.bad);
+    rmul_kernel<T><<<w.vblocks, kSolveBlock, 0, s>>>(A, out, w.Rinv, n, k);
+    PSPEC_CUDA(cudaMemcpyAsync(out, A, sizeof(T) * m, cudaMemcpyDeviceToDevice, s));
+    PSPEC_CUDA(cudaGetLastError());
+    return PSPEC_OK;
+  }
+  // M = U^T egrad, rg = egrad - U M, returns ||rg|| (synchronises)
+  pspec_status riemannian_grad(const T* U, const T* egrad, double* gnorm) {
+    PSPEC_TRY(gram(U, egrad, w.M));
+    PSPEC_TRY(combine(w.rg, egrad, 1.0, nullptr, 0.0, U, w.M, nullptr, nullptr));
+    DotPairs<T> dp{};
+    dp.x[0] = w.rg;
+    dp.y[0] = w.rg;
+    dp.np = 1;
+    PSPEC_TRY(dots(dp, w.dots));
+    double h = 0.0;
+    PSPEC_CUDA(cudaMemcpyAsync(&h, w.dots, sizeof(double), cudaMemcpyDeviceToHost, s));
+    PSPEC_CUDA(cudaStreamSynchronize(s));
+    *gnorm = std::sqrt(std::max(h, 0.0));
+    return PSPEC_OK;
+  }
+  pspec_status read_f(double* f) {
+    PSPEC_CUDA(cudaMemcpyAsync(f, w.F, sizeof(double), cudaMemcpyDeviceToHost, s));
+    PSPEC_CUDA(cudaStreamSynchronize(s));
+    return PSPEC_OK;
+  }
+};
+
+}  // namespace
+
+template <typename T>
+static pspec_status solve_impl(pspec_graph* g, int k, const double* sched, int n_p,
+                               const pspec_solve_opts& o, T* U_io, int32_t* labels,
+                               double* rcut_out, pspec_solve_stats* stats, cudaStream_t s) {
+  const auto t0 = std::chrono::steady_clock::now();
+  Solver<T> S;
+  S.g = g;
+  S.k = k;
+  S.n = g->n;
+  S.m = g->n * k;
+  S.s = s;
+  PSPEC_TRY(carve<T>(g, k, &S.w));
+  SolveWork<T>& w = S.w;
+  const int64_t m = S.m;
+  PSPEC_CUDA(cudaMemcpyAsync(w.U, U_io, sizeof(T) * m, cudaMemcpyDeviceToDevice, s));
+  PSPEC_CUDA(cudaMemsetAsync(w.bad, 0, sizeof(int), s));
+  const int chunk = sizeof(T) == 4 ? 4 : 1;  // CG iterations per host check
+  pspec_solve_stats st_local;
+  std::memset(&st_local, 0, sizeof(st_local));
+  bool all_converged = true;
+  const double Delta_bar = o.delta_bar_scale * std::sqrt((double)k);
+  for (int ip = 0; ip < n_p; ++ip) {
+    const double p = sched[ip];
+    double f = 0.0, gnorm = 0.0;
+    PSPEC_TRY(S.eval(w.U, p, w.egrad));
+    PSPEC_TRY(S.riemannian_grad(w.U, w.egrad, &gnorm));
+    PSPEC_TRY(S.read_f(&f));
+    PSPEC_TRY(take_status(g, s));
+    const double gnorm0 = gnorm;
+    double Delta = o.delta0_scale * Delta_bar;
+    int outer = 0, inner_total = 0;
+    bool converged = false;
+    while (true) {
+      if (gnorm <= std::max(o.gtol_abs, o.gtol_rel * gnorm0)) {
+        converged = true;
+        break;
+      }
+      if (outer >= o.max_outer) break;
+      ++outer;
+      // ---- truncated CG on the device
+      TcgState h{};
+      h.Delta = Delta;
+      h.rr = gnorm * gnorm;
+      h.norm_r0 = gnorm;
+      h.stop = gnorm * std::min(std::pow(gnorm, o.theta), o.kappa);
+      h.e_Pe = 0.0;
+      h.e_Pd = 0.0;
+      h.d_Pd = h.rr;
+      h.max_inner = o.max_inner;
+      PSPEC_CUDA(cudaMemcpyAsync(w.st, &h, sizeof(TcgState), cudaMemcpyHostToDevice, s));
+      PSPEC_CUDA(cudaMemsetAsync(w.eta, 0, sizeof(T) * m, s));
+      PSPEC_CUDA(cudaMemsetAsync(w.Heta, 0, sizeof(T) * m, s));
+      PSPEC_CUDA(cudaMemcpyAsync(w.r, w.rg, sizeof(T) * m, cudaMemcpyDeviceToDevice, s));
+      PSPEC_TRY(S.combine(w.delta, w.rg, -1.0, nullptr, 0.0, nullptr, nullptr, nullptr, nullptr));
+      const int* done = &w.st->done;
+      TcgState hs{};
+      for (int it = 0; it < o.max_inner; it += chunk) {
+        for (int c = 0; c < chunk && it + c < o.max_inner; ++c) {
+          PSPEC_TRY(S.hvp(w.U, w.delta, p, w.He, done));
+          PSPEC_TRY(S.gram(w.U, w.He, w.G, done));
+          {
+            TimedScope timer(g, "solve_tcg_vec", s);
+            hess_kernel<T><<<w.vblocks, kSolveBlock, 0, s>>>(w.Hd, w.He, w.U, w.G, w.delta, w.M,
+                                                              S.n, k, w.st, w.gr);
+            cg_update_kernel<T><<<w.vblocks, kSolveBlock, 0, s>>>(w.eta, w.Heta, w.r, w.delta,
+                                                                   w.Hd, m, w.st, w.gr);
+            direction_kernel<T><<<w.vblocks, kSolveBlock, 0, s>>>(w.delta, w.r, m, w.st);
+            PSPEC_CUDA(cudaGetLastError());
+          }
+        }
+        PSPEC_CUDA(cudaMemcpyAsync(&hs, w.st, sizeof(TcgState), cudaMemcpyDeviceToHost, s));
+        PSPEC_CUDA(cudaStreamSynchronize(s));
+        if (hs.done) break;
+      }
+      S.hvps += hs.j;  // HVP launches enqueued after CG stopped were no-ops
+      inner_total += hs.j;
+      const bool on_boundary = hs.boundary != 0;
+      // ---- trial point, model decrease, ratio
+      PSPEC_TRY(S.combine(w.tmp, w.U, 1.0, w.eta, 1.0, nullptr, nullptr, nullptr, nullptr));
+      PSPEC_TRY(S.qf(w.tmp, w.Unew));
+      PSPEC_TRY(S.eval(w.Unew, p, w.egrad_new));
+      DotPairs<T> dp{};
+      dp.x[0] = w.rg;
+      dp.y[0] = w.eta;
+      dp.x[1] = w.eta;
+      dp.y[1] = w.Heta;
+      dp.np = 2;
+      PSPEC_TRY(S.dots(dp, w.dots));
+      double dv[2] = {0, 0};
+      double f_new = 0.0;
+      PSPEC_CUDA(cudaMemcpyAsync(dv, w.dots, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+      PSPEC_TRY(S.read_f(&f_new));
+      // a trial point whose evaluation met a NaN/Inf or a zero column is rejected
+      const bool trial_bad = take_status(g, s) != PSPEC_OK || !std::isfinite(f_new);
+      const double reg = o.rho_reg * std::max(1.0, std::fabs(f));
+      const double num = f - f_new + reg;
+      const double den = -(dv[0] + 0.5 * dv[1]) + reg;
+      const bool model_decreased = den >= 0.0 && !trial_bad;
+      const double rho = trial_bad ? NAN : (den != 0.0 ? num / den : -INFINITY);
+      if (!model_decreased || rho < 0.25 || std::isnan(rho))
+        Delta *= 0.25;
+      else if (rho > 0.75 && on_boundary)
+        Delta = std::min(2.0 * Delta, Delta_bar);
+      const bool accept = model_decreased && rho > o.rho_prime;
+      if (o.verbose)
+        std::fprintf(stderr, "pspec p=%.3f it=%d f=%.10e |g|=%.3e tcg=%d(%d) rho=%.3f Delta=%.3e %s\n", p,
+                     outer, f, gnorm, hs.j, hs.reason, rho, Delta, accept ? "acc" : "rej");
+      if (accept) {
+        std::swap(w.U, w.Unew);
+        std::swap(w.egrad, w.egrad_new);
+        f = f_new;
+        PSPEC_TRY(S.riemannian_grad(w.U, w.egrad, &gnorm));
+      }
+    }
+    if (!converged) all_converged = false;
+    if (ip < 32) {
+      st_local.outer[ip] = outer;
+      st_local.inner[ip] = inner_total;
+      st_local.f[ip] = f;
+      st_local.gnorm[ip] = gnorm;
+    }
+  }
+  st_local.n_stages = n_p;
+  PSPEC_CUDA(cudaMemcpyAsync(U_io, w.U, sizeof(T) * m, cudaMemcpyDeviceToDevice, s));
+  int bad = 0;
+  PSPEC_CUDA(cudaMemcpyAsync(&bad, w.bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PSPEC_CUDA(cudaStreamSynchronize(s));
+  if (bad) return set_error(PSPEC_ERR_NONFINITE, "Cholesky-QR met a Gram matrix that is not positive definite");
+  // ---- k-means on the rows of U, then RCut
+  if (labels || rcut_out) {
+    int32_t* lab = labels;
+    void* tmp_lab = nullptr;
+    if (!lab) {
+      PSPEC_CUDA(cudaMalloc(&tmp_lab, sizeof(int32_t) * g->n));
+      lab = (int32_t*)tmp_lab;
+    }
+    double inertia = 0.0;
+    pspec_status ks = pspec_kmeans(U_io, g->n, k, sizeof(T) == 4 ? PSPEC_F32 : PSPEC_F64, k, o.seed,
+                                   o.kmeans_restarts, o.kmeans_max_iter, lab, nullptr, &inertia, s);
+    st_local.kmeans_inertia = inertia;
+    if (ks == PSPEC_OK && rcut_out) ks = pspec_rcut(g, lab, k, rcut_out, s);
+    if (tmp_lab) cudaFree(tmp_lab);
+    if (ks != PSPEC_OK) return ks;
+  }
+  st_local.eval_calls = S.evals;
+  st_local.hvp_calls = S.hvps;
+  st_local.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = st_local;
+  return all_converged ? PSPEC_OK : set_error(PSPEC_ERR_NOT_CONVERGED, "a stage reached max_outer");
+}
+
+}  // namespace pspec
+
+using namespace pspec;
+
+extern "C" void pspec_solve_opts_default(pspec_solve_opts* o) {
+  if (!o) return;
+  o->max_outer = 30;
+  o->max_inner = 50;
+  o->gtol_rel = 1e-6;
+  o->gtol_abs = 0.0;
+  o->theta = 1.0;
+  o->kappa = 0.1;
+  o->delta_bar_scale = 1.0;
+  o->delta0_scale = 0.1;
+  o->rho_prime = 0.1;
+  o->rho_reg = 1e-10;
+  o->kmeans_restarts = 10;
+  o->kmeans_max_iter = 300;
+  o->seed = 0;
+  o->verbose = 0;
+}
+
+extern "C" pspec_status pspec_solve(pspec_graph* g, int k, const double* p_schedule, int n_p,
+                                    const pspec_solve_opts* opts, pspec_dtype dtype, void* U_inout,
+                                    int32_t* labels_out, double* rcut_out, pspec_solve_stats* stats,
+                                    void* stream) {
+  if (!g) return set_error(PSPEC_ERR_INVALID_ARG, "graph is NULL");
+  if (g->n_graphs != 1) return set_error(PSPEC_ERR_INVALID_ARG, "pspec_solve takes a single graph");
+  if (k < 1 || k > kMaxK) return set_error(PSPEC_ERR_INVALID_ARG, "k must be in [1, 16]");
+  if (k > g->n) return set_error(PSPEC_ERR_INVALID_ARG, "k exceeds n");
+  if (!p_schedule || n_p < 1) return set_error(PSPEC_ERR_INVALID_ARG, "empty p schedule");
+  for (int i = 0; i < n_p; ++i) {
+    if (!(p_schedule[i] > 1.0 && p_schedule[i] <= 2.0))
+      return set_error(PSPEC_ERR_INVALID_ARG, "every p must be in (1, 2]");
+    if (i > 0 && p_schedule[i] > p_schedule[i - 1])
+      return set_error(PSPEC_ERR_INVALID_ARG, "the p schedule must be non-increasing");
+  }
+  pspec_solve_opts o;
+  pspec_solve_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.max_inner < 1 || o.max_outer < 0 || o.kmeans_restarts < 1)
+    return set_error(PSPEC_ERR_INVALID_ARG, "bad iteration caps");
+  PSPEC_TRY(check_block(U_inout, k, dtype, "U_inout"));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dtype == PSPEC_F32)
+    return solve_impl<float>(g, k, p_schedule, n_p, o, (float*)U_inout, labels_out, rcut_out, stats, s);
+  if (dtype == PSPEC_F64)
+    return solve_impl<double>(g, k, p_schedule, n_p, o, (double*)U_inout, labels_out, rcut_out, stats, s);
+  return set_error(PSPEC_ERR_INVALID_ARG, "bad dtype");
+}

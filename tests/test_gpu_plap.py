@@ -1,0 +1,186 @@
+"""GPU parity of pspec_eval / pspec_hvp against the FP64 oracle.
+
+The oracle receives exactly the FP32 values the GPU receives (U, V and W
+widened to float64), so differences come from the kernels' arithmetic only.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_common import TOL_F, TOL_F64, TOL_GRAD, TOL_HVP, rel_col, small_graphs
+from paper_2605_26975_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2605_26975_gb300 import build
+    build.build()
+    from paper_2605_26975_gb300 import api as A
+    return A
+
+
+@pytest.fixture(scope="module")
+def graphs(api):
+    out = {}
+    for name, g in small_graphs().items():
+        out[name] = (g, api.Graph.from_csr(g))
+    return out
+
+
+def blocks(n, k, seed):
+    U = wl.orthonormal_block(seed, n, k, np.float32)
+    V = wl.gaussian_block(seed + 1, n, k, dtype=np.float32)
+    return U, V
+
+
+def check_eval(api, g, G, U, p):
+    Ud = torch.from_numpy(U).cuda()
+    F, grad, parts = G.eval(Ud, p, parts=True)
+    torch.cuda.synchronize()
+    assert G.status() == 0
+    U64 = U.astype(np.float64)
+    F_ref = oracle.objective(g, U64, p)
+    N, D = oracle.objective_parts(g, U64, p)
+    gr_ref = oracle.euclidean_grad(g, U64, p)
+    assert abs(F.item() - F_ref) <= TOL_F * abs(F_ref)
+    P = parts.cpu().numpy()
+    k = U.shape[1]
+    assert np.allclose(P[:k], N, rtol=TOL_F, atol=0)
+    assert np.allclose(P[k:], D, rtol=TOL_F, atol=0)
+    assert rel_col(grad.cpu().numpy(), gr_ref) <= TOL_GRAD
+
+
+def check_hvp(api, g, G, U, V, p):
+    Ud = torch.from_numpy(U).cuda()
+    Vd = torch.from_numpy(V).cuda()
+    HV = G.hvp(Ud, Vd, p)
+    torch.cuda.synchronize()
+    assert G.status() == 0
+    ref = oracle.euclidean_hvp(g, U.astype(np.float64), V.astype(np.float64), p)
+    assert rel_col(HV.cpu().numpy(), ref) <= TOL_HVP
+
+
+@pytest.mark.parametrize("name", ["sbm", "grid", "knn", "hubs", "isolated"])
+@pytest.mark.parametrize("k", [1, 3, 4, 8, 16])
+@pytest.mark.parametrize("p", [2.0, 1.5, 1.1])
+def test_eval_and_hvp_match_oracle(api, graphs, name, k, p):
+    g, G = graphs[name]
+    U, V = blocks(g.n, k, 100 + k)
+    check_eval(api, g, G, U, p)
+    check_hvp(api, g, G, U, V, p)
+
+
+@pytest.mark.parametrize("k", [2, 5, 6, 7, 9, 10, 11, 12, 13, 14, 15])
+def test_every_k(api, graphs, k):
+    g, G = graphs["sbm"]
+    U, V = blocks(g.n, k, 7 * k)
+    check_eval(api, g, G, U, 1.3)
+    check_hvp(api, g, G, U, V, 1.3)
+
+
+@pytest.mark.parametrize("p", [2.0, 1.7, 1.2])
+def test_ties_and_zeros(api, graphs, p):
+    # quantised values: many exact zero differences and exact zero entries
+    g, G = graphs["sbm"]
+    rng = np.random.default_rng(9)
+    U = (rng.integers(-3, 4, size=(g.n, 4)) * 0.25).astype(np.float32)
+    V = rng.standard_normal((g.n, 4)).astype(np.float32)
+    check_eval(api, g, G, U, p)
+    check_hvp(api, g, G, U, V, p)
+
+
+@pytest.mark.parametrize("k", [1, 4, 8])
+def test_plain_fp64_path(api, graphs, k):
+    g, G = graphs["hubs"]
+    U, V = blocks(g.n, k, 55)
+    U64, V64 = U.astype(np.float64), V.astype(np.float64)
+    Ud = torch.from_numpy(U64).cuda()
+    Vd = torch.from_numpy(V64).cuda()
+    for p in (2.0, 1.4):
+        F, grad = G.eval(Ud, p)
+        HV = G.hvp(Ud, Vd, p)
+        torch.cuda.synchronize()
+        assert abs(F.item() - oracle.objective(g, U64, p)) <= TOL_F64 * abs(F.item())
+        assert rel_col(grad.cpu().numpy(), oracle.euclidean_grad(g, U64, p)) <= TOL_F64
+        assert rel_col(HV.cpu().numpy(), oracle.euclidean_hvp(g, U64, V64, p)) <= 1e-10
+
+
+def test_bit_reproducible(api, graphs):
+    g, G = graphs["hubs"]
+    U, V = blocks(g.n, 8, 77)
+    Ud = torch.from_numpy(U).cuda()
+    Vd = torch.from_numpy(V).cuda()
+    F1, g1 = G.eval(Ud, 1.3)
+    h1 = G.hvp(Ud, Vd, 1.3)
+    F2, g2 = G.eval(Ud, 1.3)
+    h2 = G.hvp(Ud, Vd, 1.3)
+    torch.cuda.synchronize()
+    assert F1.item() == F2.item()
+    assert torch.equal(g1, g2) and torch.equal(h1, h2)
+
+
+def test_host_pointer_path_matches_device(api, graphs):
+    g, G = graphs["knn"]
+    U, V = blocks(g.n, 8, 31)
+    Uh = torch.from_numpy(U).pin_memory()
+    Vh = torch.from_numpy(V).pin_memory()
+    gh = torch.empty_like(Uh).pin_memory()
+    hh = torch.empty_like(Uh).pin_memory()
+    F_host = G.eval_host(Uh, 1.5, gh)
+    G.hvp_host(Uh, Vh, 1.5, hh)
+    F, grad = G.eval(Uh.cuda(), 1.5)
+    HV = G.hvp(Uh.cuda(), Vh.cuda(), 1.5)
+    torch.cuda.synchronize()
+    assert F_host == F.item()
+    assert torch.equal(gh, grad.cpu()) and torch.equal(hh, HV.cpu())
+
+
+def test_single_vertex_and_empty_graph(api):
+    g = wl.CSRGraph(1, np.array([0, 0], dtype=np.int64), np.zeros(0, np.int32),
+                    np.zeros(0, np.float32))
+    G = api.Graph.from_csr(g)
+    U = torch.tensor([[0.7]], device="cuda")
+    F, grad = G.eval(U, 1.5)
+    HV = G.hvp(U, torch.tensor([[1.0]], device="cuda"), 1.5)
+    torch.cuda.synchronize()
+    assert F.item() == 0.0
+    assert grad.item() == 0.0
+    ref = oracle.euclidean_hvp(g, np.array([[0.7]]), np.array([[1.0]]), 1.5)
+    assert abs(HV.item() - ref[0, 0]) <= 1e-5 * abs(ref[0, 0])
+
+
+def test_zero_column_and_nonfinite_are_reported(api, graphs):
+    from paper_2605_26975_gb300 import _abi
+    g, G = graphs["sbm"]
+    U, _ = blocks(g.n, 4, 3)
+    U[:, 2] = 0.0
+    G.eval(torch.from_numpy(U).cuda(), 1.5)
+    assert G.status() == _abi.PSPEC_ERR_ZERO_COLUMN
+    U, _ = blocks(g.n, 4, 3)
+    U[10, 1] = np.nan
+    G.eval(torch.from_numpy(U).cuda(), 1.5)
+    assert G.status() == _abi.PSPEC_ERR_NONFINITE
+    # the status word is cleared once read
+    U, _ = blocks(g.n, 4, 3)
+    G.eval(torch.from_numpy(U).cuda(), 1.5)
+    assert G.status() == 0
+
+
+def test_invalid_arguments(api, graphs):
+    from paper_2605_26975_gb300 import _abi
+    g, G = graphs["sbm"]
+    U = torch.zeros((g.n, 4), device="cuda")
+    for p in (1.0, 2.5, float("nan")):
+        with pytest.raises(_abi.PspecError):
+            G.eval(U, p)
+    with pytest.raises(_abi.PspecError):
+        G.eval(torch.zeros((g.n, 17), device="cuda"), 1.5)
+    # misaligned block: a view that starts one float into a 16-byte-aligned buffer
+    buf = torch.zeros(g.n * 4 + 1, device="cuda")
+    with pytest.raises(_abi.PspecError):
+        G.eval(buf[1:].view(g.n, 4), 1.5)
