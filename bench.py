@@ -171,19 +171,44 @@ def dist_env():
     return world, rank, local
 
 
+def job_throughput(ms_local, edge_cols_local, dist=None):
+    """Whole-job throughput of independent replicas: every rank's step time is
+    reduced with MAX (the job is as slow as its slowest rank) and the units
+    of all ranks are summed.  Returns (value, ms_max)."""
+    import torch
+    world = 1
+    ms = float(ms_local)
+    units = float(edge_cols_local)
+    if dist is not None and dist.is_initialized():
+        world = dist.get_world_size()
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        u = torch.tensor([units], dtype=torch.float64, device=dev)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        ms, units = t.item(), u.item()
+    return units / (ms * 1e-3), ms
+
+
+def replica_seeds(name, rank):
+    """Graph and block seeds of rank `rank`'s replica (rank 0: the named workload)."""
+    idx = wl.WORKLOADS[name]["index"]
+    return 1000 + idx + 100 * rank, 2000 + idx + 100 * rank, 3000 + idx + 100 * rank
+
+
 def build_workload(name, seed_shift=0):
     info = wl.WORKLOADS[name]
     if seed_shift == 0:
         g = wl.make_graph(name)
         U, V = wl.make_blocks(name, g.n, info["k"])
     else:  # an independent replica for rank > 0
-        idx = info["index"]
+        gs, us, vs = replica_seeds(name, seed_shift)
         g = {"knn_gmm": lambda s: wl.knn_gaussian_mixture(s),
              "grid3d": lambda s: wl.grid3d_longrange(s),
              "dcsbm": lambda s: wl.dcsbm_powerlaw(s),
-             "sbm4": lambda s: wl.sbm_bernoulli(s)}[name](1000 + idx + 100 * seed_shift)
-        U = wl.orthonormal_block(2000 + idx + 100 * seed_shift, g.n, info["k"])
-        V = wl.gaussian_block(3000 + idx + 100 * seed_shift, g.n, info["k"])
+             "sbm4": lambda s: wl.sbm_bernoulli(s)}[name](gs)
+        U = wl.orthonormal_block(us, g.n, info["k"])
+        V = wl.gaussian_block(vs, g.n, info["k"])
     return g, U, V, info
 
 
@@ -290,13 +315,9 @@ def main():
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
-    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
+    ms_local = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps
     edge_cols = 2 * g.nnz * k
-    value = world * edge_cols / (ms * 1e-3)
+    value, ms = job_throughput(ms_local, edge_cols, dist if world > 1 else None)
 
     # ---- per-kernel device times (same steps, library events on the stream)
     G.set_timing(True)

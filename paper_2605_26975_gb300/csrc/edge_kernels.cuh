@@ -9,39 +9,69 @@
 //           Delta_i                                              -> out_b
 //         and sigma_N = sum_i Delta_i v_i, sigma_D = sum_i phi_p(u_i) v_i.
 //
-// One pass over the CSR: every stored entry (i, j) costs one lg2 and one ex2
-// per column, w_ij |d|^(p-2) = 2^((p-2) log2|d| + log2 w_ij) with log2 w
-// computed once per entry, then phi = that * d and |d|^p = phi * d.  An exact
-// zero difference gives phi = 0 (the log is clamped, see common.cuh) and, for
-// p < 2, no curvature term in S.
+// Arithmetic.  Every stored entry (i, j) costs one lg2 and one ex2 per column:
+// w_ij |d|^(p-2) = 2^((p-2) log2|d| + log2 w_ij) with log2 w computed once per
+// entry, then phi = that * d and |d|^p = phi * d.  An exact zero difference
+// gives phi = 0 (the log is clamped, see common.cuh) and, for p < 2, no
+// curvature term in S.
 //
-// Work decomposition: each warp walks warp tasks (TaskSet) in a fixed
-// grid-stride order.  A task's rows are handled by teams of E edge slots x Q
-// column lanes; a lane owns CPL = K/Q columns loaded as 16/8/4-byte vectors,
-// so the gather of a neighbour row is one or a few vector loads.  Row sums are
-// reduced across the E slots by warp shuffles; per-column objective sums are
-// folded across teams and kept per warp in compensated (Kahan) FP32 in shared
-// memory, then reduced across warps and blocks in float-float.  Long rows are
-// split into chunks whose partial row sums the warp finishing the row's last
-// chunk adds in chunk order.  Nothing depends on scheduling order, so every
-// result is bit-reproducible run to run.
+// Data movement.  The kernels read a copy of W whose rows are stably sorted
+// by degree (perm maps a sorted row back to its vertex).  A warp task is a run
+// of consecutive sorted rows of one degree, so its entries are contiguous.
+// Each warp owns a ring of kStages shared-memory stages; lane 0 fills a stage
+// with the task's column indices, weights and perm slice by three TMA bulk
+// copies completing on the stage's mbarrier, kStages tasks ahead of use, so
+// the CSR stream never stalls the lanes: they wait only on the 16-byte
+// gathers of neighbour rows of U (and V).  All barrier waits are bounded; a
+// wait that gives up records a timeout in the status word and the warp stops.
+//
+// Work split.  A row is handled by a team of E edge slots x Q column lanes; a
+// lane owns CPL = K/Q consecutive columns (16/8/4-byte vectors).  Typical rows
+// get E = 1 (a lane walks its row UNR entries at a time, no shuffles); longer
+// rows are shared by E slots and reduced by warp shuffles; rows above the hub
+// threshold are split into chunks whose partial sums the warp finishing the
+// row's last chunk adds in chunk order (atomic ticket, no spinning).
+// Per-column sums live per lane in registers (compensated for the objective),
+// then are reduced across the warp, block and grid in float-float in a fixed
+// order, so every result is bit-reproducible run to run.
 #pragma once
 
 #include "common.cuh"
 
 namespace pspec {
 
+// Entries per lane per row before a row gets more edge slots: 8*Q, so the
+// largest task (32/Q lanes x that) is 256 entries for every column split.
+__host__ __device__ constexpr int edges_per_lane(int Q) { return 8 * Q; }
+__host__ __device__ constexpr int task_max_entries(int Q) { return 32 * edges_per_lane(Q) / Q; }
+constexpr int kStages = 3;
+constexpr uint32_t kWaitTries = 1u << 20;
+
+template <int Q>
+struct StageBuf {
+  static constexpr int SEG = task_max_entries(Q) + 8;  // + alignment slack
+  int4 desc;
+  int32_t col[SEG];
+  float val[SEG];
+  int32_t perm[40];
+};
+
+template <int Q>
+__host__ __device__ constexpr size_t edge_smem_bytes() {
+  return sizeof(StageBuf<Q>) * kStages * kWarps + sizeof(uint64_t) * kStages * kWarps;
+}
+
 struct EdgeArgs {
-  const int64_t* rowptr;
+  const int64_t* rowptr;  // degree-sorted rows
   const int32_t* col;
   const float* val;
+  const int32_t* perm;    // sorted row -> vertex
   const float* U;
   const float* V;
   float* out_a;
   float* out_b;
   const int4* tasks;
   int n_tasks;
-  int chunk_edges;
   float* hub_part;
   const int32_t* hub_first;
   const int32_t* hub_nchunk;
@@ -67,6 +97,48 @@ __device__ __forceinline__ void store_row(float* base, int64_t row, int c0, cons
   for (int j = 0; j < CPL; j += VW) store_vec<VW>(base + row * K + c0 + j, src + j);
 }
 
+// per-lane accumulator: compensated for the objective's sums, plain for the
+// Hessian product's (whose rank-two coefficients need ~1e-6 only)
+template <bool COMP> struct LaneAcc;
+template <> struct LaneAcc<true> {
+  Kahan k;
+  __device__ __forceinline__ void init() { k.init(); }
+  __device__ __forceinline__ void add(float x) { k.add(x); }
+  __device__ __forceinline__ float2 ff() const { return kahan_to_ff(k); }
+};
+template <> struct LaneAcc<false> {
+  float s;
+  __device__ __forceinline__ void init() { s = 0.f; }
+  __device__ __forceinline__ void add(float x) { s += x; }
+  __device__ __forceinline__ float2 ff() const { return make_float2(s, 0.f); }
+};
+
+// task descriptor fields (see ensure_tasks)
+__device__ __forceinline__ bool task_is_hub(int4 t) { return ((t.z >> 8) & 1) != 0; }
+__device__ __forceinline__ int task_entries(int4 t) {
+  return task_is_hub(t) ? (t.z >> 10) : (t.y & 0xff) * (t.y >> 8);
+}
+__device__ __forceinline__ int task_rows(int4 t) { return task_is_hub(t) ? 1 : (t.y & 0xff); }
+
+// lane 0: start the three bulk copies of task t into stage st.  Windows are
+// widened to 16-byte granules (the arrays are padded past their ends).
+template <int Q>
+__device__ __forceinline__ void issue_stage(const EdgeArgs& a, int4 t, StageBuf<Q>* st, uint64_t* bar) {
+  st->desc = t;
+  const int cnt = task_entries(t);
+  const int nr = task_rows(t);
+  const int oc = t.w & 3;  // entries before the task in its first granule
+  const int op = t.x & 3;
+  const uint32_t bc = (uint32_t)((oc + cnt + 3) & ~3) * 4u;
+  const uint32_t bp = (uint32_t)((op + nr + 3) & ~3) * 4u;
+  mbar_arrive_expect_tx(bar, (cnt > 0 ? 2u * bc : 0u) + bp);
+  if (cnt > 0) {
+    tma_load_1d(st->col, a.col + (t.w - oc), bc, bar);
+    tma_load_1d(st->val, a.val + (t.w - oc), bc, bar);
+  }
+  tma_load_1d(st->perm, a.perm + (t.x - op), bp, bar);
+}
+
 template <int K, bool HVP>
 __global__ void __launch_bounds__(kBlock) edge_kernel(EdgeArgs a) {
   constexpr int Q = q_of(K);
@@ -74,14 +146,20 @@ __global__ void __launch_bounds__(kBlock) edge_kernel(EdgeArgs a) {
   constexpr int VW = vw_of(K);
   constexpr int NQ = HVP ? 4 : 2;  // N, D (, sigma_N, sigma_D)
   constexpr int NV = NQ * K;
+  constexpr int UNR = HVP ? (CPL > 8 ? 1 : 2) : (CPL > 8 ? 2 : 4);  // entries per lane per trip
+  constexpr bool COMP = !HVP;
 
   if (a.skip && *a.skip) return;  // uniform over the grid
-  __shared__ float s_acc[kWarps][NV][2];  // per-warp Kahan (sum, compensation)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ float2 s_warp[kWarps][NV];
   __shared__ float2 s_blk[NV];
   __shared__ float2 s_tot[NV];
 
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
+  StageBuf<Q>* stages = reinterpret_cast<StageBuf<Q>*>(smem_raw) + wib * kStages;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + sizeof(StageBuf<Q>) * kStages * kWarps) +
+                   wib * kStages;
   const int q = lane % Q;
   const int c0 = q * CPL;
   const int gwarp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
@@ -89,37 +167,65 @@ __global__ void __launch_bounds__(kBlock) edge_kernel(EdgeArgs a) {
   const float pm2 = a.pm2;
   const bool zero_rule = pm2 != 0.0f;  // p < 2: a zero difference has no curvature
 
-  for (int i = lane; i < NV; i += 32) {
-    s_acc[wib][i][0] = 0.f;
-    s_acc[wib][i][1] = 0.f;
+  LaneAcc<COMP> accN[CPL], accD[CPL];
+  LaneAcc<false> accCN[HVP ? CPL : 1], accCD[HVP ? CPL : 1];
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) {
+    accN[c].init();
+    accD[c].init();
+    if constexpr (HVP) {
+      accCN[c].init();
+      accCD[c].init();
+    }
+  }
+
+  // ---- prologue: barriers, then the first kStages tasks of this warp in flight
+  if (lane == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+    mbar_init_fence();
+    for (int s = 0; s < kStages; ++s) {
+      const int t = gwarp + s * nwarps;
+      if (t < a.n_tasks) issue_stage<Q>(a, __ldg(&a.tasks[t]), &stages[s], &bars[s]);
+    }
   }
   __syncwarp();
 
-  for (int t = gwarp; t < a.n_tasks; t += nwarps) {
-    const int4 task = __ldg(&a.tasks[t]);
+  uint32_t phase = 0;  // bit s: parity of the next completion of stage s
+  bool timed_out = false;
+  int it = 0;
+  for (int t = gwarp; t < a.n_tasks; t += nwarps, ++it) {
+    const int s = it % kStages;
+    // every lane observes the completion itself (acquire); the decision to go
+    // on is taken by the whole warp
+    const bool got = mbar_wait_bounded(&bars[s], (phase >> s) & 1u, kWaitTries);
+    if (!__all_sync(0xffffffffu, got)) {
+      timed_out = true;
+      break;
+    }
+    phase ^= 1u << s;
+    StageBuf<Q>& st = stages[s];
+    const int4 task = st.desc;
+    const bool hub = task_is_hub(task);
     const int elog = task.z & 0xff;
-    const bool hub = (task.z >> 8) != 0;
     const int E = 1 << elog;
     const int T = E * Q;
     const int team = lane / T;
     const int slot = (lane % T) / Q;
-    int64_t row, e_beg = 0, e_end = 0;
+    const int oc = task.w & 3;
+    const int op = task.x & 3;
+    int l_beg, l_end;  // entries of this lane's row within the stage
     bool active;
     if (!hub) {
-      row = (int64_t)task.x + team;
-      active = team < task.y;
-      if (active) {
-        e_beg = __ldg(&a.rowptr[row]);
-        e_end = __ldg(&a.rowptr[row + 1]);
-      }
+      const int deg = task.y >> 8;
+      active = team < (task.y & 0xff);
+      l_beg = oc + team * deg;
+      l_end = l_beg + deg;
     } else {
-      row = task.x;
       active = true;
-      const int64_t rb = __ldg(&a.rowptr[row]);
-      const int64_t re = __ldg(&a.rowptr[row + 1]);
-      e_beg = rb + (int64_t)task.y * a.chunk_edges;
-      e_end = min(re, e_beg + (int64_t)a.chunk_edges);
+      l_beg = oc;
+      l_end = oc + (task.z >> 10);
     }
+    const int64_t row = active ? (int64_t)st.perm[op + (hub ? 0 : team)] : 0;
 
     float ui[CPL], vi[CPL], dsum[CPL], nsum[CPL], ssum[CPL];
 #pragma unroll
@@ -127,41 +233,48 @@ __global__ void __launch_bounds__(kBlock) edge_kernel(EdgeArgs a) {
     if (active) {
       load_row<K, CPL, VW>(a.U, row, c0, ui);
       if constexpr (HVP) load_row<K, CPL, VW>(a.V, row, c0, vi);
-      for (int64_t e = e_beg + slot; e < e_end; e += 2 * E) {
-        const int64_t e2 = e + E;
-        const bool has2 = e2 < e_end;
-        const int j1 = __ldg(&a.col[e]);
-        const float w1 = __ldg(&a.val[e]);
-        const int j2 = has2 ? __ldg(&a.col[e2]) : j1;
-        const float w2 = has2 ? __ldg(&a.val[e2]) : 0.0f;  // weight 0: contributes nothing
-        float uj1[CPL], uj2[CPL], vj1[CPL], vj2[CPL];
-        load_row<K, CPL, VW>(a.U, j1, c0, uj1);
-        load_row<K, CPL, VW>(a.U, j2, c0, uj2);
-        if constexpr (HVP) {
-          load_row<K, CPL, VW>(a.V, j1, c0, vj1);
-          load_row<K, CPL, VW>(a.V, j2, c0, vj2);
-        }
-        const float lw1 = lg2_approx(w1);
-        const float lw2 = lg2_approx(w2);
+      for (int e = l_beg + slot; e < l_end; e += UNR * E) {
+        int jj[UNR];
+        float lw[UNR];
 #pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-          const float d1 = ui[c] - uj1[c];
-          const float d2 = ui[c] - uj2[c];
-          const float sw1 = ex2_approx(fmaf(pm2, fmaxf(lg2_approx(fabsf(d1)), -126.0f), lw1));
-          const float sw2 = ex2_approx(fmaf(pm2, fmaxf(lg2_approx(fabsf(d2)), -126.0f), lw2));
-          const float ph1 = sw1 * d1;  // w phi_p(d)
-          const float ph2 = sw2 * d2;
-          dsum[c] += ph1;
-          dsum[c] += ph2;
-          nsum[c] = fmaf(ph1, d1, nsum[c]);  // w |d|^p
-          nsum[c] = fmaf(ph2, d2, nsum[c]);
-          if constexpr (HVP) {
-            const float s1 = (zero_rule && d1 == 0.0f) ? 0.0f : sw1;
-            const float s2 = (zero_rule && d2 == 0.0f) ? 0.0f : sw2;
-            ssum[c] = fmaf(s1, vi[c] - vj1[c], ssum[c]);
-            ssum[c] = fmaf(s2, vi[c] - vj2[c], ssum[c]);
+        for (int u = 0; u < UNR; ++u) {
+          const int eu = e + u * E;
+          const bool ok = eu < l_end;
+          jj[u] = ok ? st.col[eu] : (int)row;  // off the end: own row, weight 0
+          lw[u] = ok ? st.val[eu] : 0.0f;
+        }
+        float uj[UNR][CPL], vj[UNR][CPL];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+          load_row<K, CPL, VW>(a.U, jj[u], c0, uj[u]);
+          if constexpr (HVP) load_row<K, CPL, VW>(a.V, jj[u], c0, vj[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) lw[u] = lg2_approx(lw[u]);  // log2 0 = -inf: no contribution
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) {
+            const float d = ui[c] - uj[u][c];
+            const float sw = ex2_approx(fmaf(pm2, fmaxf(lg2_approx(fabsf(d)), -126.0f), lw[u]));
+            const float ph = sw * d;  // w phi_p(d)
+            dsum[c] += ph;
+            nsum[c] = fmaf(ph, d, nsum[c]);  // w |d|^p
+            if constexpr (HVP) {
+              const float sz = (zero_rule && d == 0.0f) ? 0.0f : sw;
+              ssum[c] = fmaf(sz, vi[c] - vj[u][c], ssum[c]);
+            }
           }
         }
+      }
+    }
+    // every lane has read the stage: refill it with this warp's task kStages ahead
+    __syncwarp();
+    if (lane == 0) {
+      const int tn = t + kStages * nwarps;
+      if (tn < a.n_tasks) {
+        fence_proxy_async_smem();
+        issue_stage<Q>(a, __ldg(&a.tasks[tn]), &st, &bars[s]);
       }
     }
     // row sums across the E edge slots of each team (lanes of equal q)
@@ -174,35 +287,32 @@ __global__ void __launch_bounds__(kBlock) edge_kernel(EdgeArgs a) {
       }
     }
     const bool lead = active && slot == 0;
-    // per-row vertex terms on the lead lanes; everything else contributes 0
-    float dpart[CPL], cnpart[CPL], cdpart[CPL];
+    const bool first_chunk = !hub || ((task.z >> 9) & 1);
+    if (lead) {
 #pragma unroll
-    for (int c = 0; c < CPL; ++c) {
-      dpart[c] = 0.f; cnpart[c] = 0.f; cdpart[c] = 0.f;
-      if (!lead) nsum[c] = 0.f;
-    }
-    const bool vertex = lead && (!hub || task.y == 0);
-    if (vertex) {
+      for (int c = 0; c < CPL; ++c) accN[c].add(nsum[c]);
+      if (first_chunk) {  // vertex terms once per row
 #pragma unroll
-      for (int c = 0; c < CPL; ++c) {
-        const float phu = abs_pow_pm2_clamped(ui[c], pm2) * ui[c];  // phi_p(u_i)
-        dpart[c] = phu * ui[c];                                     // |u_i|^p
-        if constexpr (HVP) cdpart[c] = phu * vi[c];
+        for (int c = 0; c < CPL; ++c) {
+          const float phu = abs_pow_pm2_clamped(ui[c], pm2) * ui[c];  // phi_p(u_i)
+          accD[c].add(phu * ui[c]);                                   // |u_i|^p
+          if constexpr (HVP) accCD[c].add(phu * vi[c]);
+        }
       }
-    }
-    if (lead && !hub) {
-      if constexpr (HVP) {
-        store_row<K, CPL, VW>(a.out_a, row, c0, ssum);
-        store_row<K, CPL, VW>(a.out_b, row, c0, dsum);
+      if (!hub) {
+        if constexpr (HVP) {
+          store_row<K, CPL, VW>(a.out_a, row, c0, ssum);
+          store_row<K, CPL, VW>(a.out_b, row, c0, dsum);
 #pragma unroll
-        for (int c = 0; c < CPL; ++c) cnpart[c] = dsum[c] * vi[c];
-      } else {
-        store_row<K, CPL, VW>(a.out_a, row, c0, dsum);
+          for (int c = 0; c < CPL; ++c) accCN[c].add(dsum[c] * vi[c]);
+        } else {
+          store_row<K, CPL, VW>(a.out_a, row, c0, dsum);
+        }
       }
     }
     if (hub) {
       // publish this chunk's partial row sums; the last chunk adds them up
-      const int slot_id = task.w;
+      const int slot_id = task.y;
       if (lead) {
         float* hp = a.hub_part + (size_t)slot_id * 2 * K;
 #pragma unroll
@@ -240,7 +350,7 @@ __global__ void __launch_bounds__(kBlock) edge_kernel(EdgeArgs a) {
             store_row<K, CPL, VW>(a.out_a, row, c0, rs);
             store_row<K, CPL, VW>(a.out_b, row, c0, rd);
 #pragma unroll
-            for (int c = 0; c < CPL; ++c) cnpart[c] = rd[c] * vi[c];
+            for (int c = 0; c < CPL; ++c) accCN[c].add(rd[c] * vi[c]);
           } else {
             store_row<K, CPL, VW>(a.out_a, row, c0, rd);
           }
@@ -248,42 +358,49 @@ __global__ void __launch_bounds__(kBlock) edge_kernel(EdgeArgs a) {
         if (lane == 0) a.hub_ticket[h] = 0u;
       }
     }
-    // fold the task's per-column sums across teams, then into the warp's
-    // compensated accumulators (lanes 0..Q-1 own distinct columns)
-    for (int off = T; off < 32; off <<= 1) {
-#pragma unroll
-      for (int c = 0; c < CPL; ++c) {
-        nsum[c] += __shfl_xor_sync(0xffffffffu, nsum[c], off);
-        dpart[c] += __shfl_xor_sync(0xffffffffu, dpart[c], off);
-        if constexpr (HVP) {
-          cnpart[c] += __shfl_xor_sync(0xffffffffu, cnpart[c], off);
-          cdpart[c] += __shfl_xor_sync(0xffffffffu, cdpart[c], off);
-        }
-      }
-    }
-    if (lane < Q) {
-#pragma unroll
-      for (int c = 0; c < CPL; ++c) {
-        const float vals[4] = {nsum[c], dpart[c], cnpart[c], cdpart[c]};
-#pragma unroll
-        for (int qq = 0; qq < NQ; ++qq) {
-          float* acc = s_acc[wib][qq * K + c0 + c];
-          const float y = vals[qq] - acc[1];
-          const float tt = acc[0] + y;
-          acc[1] = (tt - acc[0]) - y;
-          acc[0] = tt;
-        }
+  }
+  if (timed_out) {
+    // drain this warp's copies still in flight (bounded), then report
+    if (lane == 0) {
+      atomicOr(a.status, kStatusTimeout);
+      int t = gwarp + it * nwarps;
+      for (int k2 = 0; k2 < kStages && t < a.n_tasks; ++k2, ++it, t += nwarps) {
+        const int s = it % kStages;
+        mbar_wait_bounded(&bars[s], (phase >> s) & 1u, kWaitTries);
+        phase ^= 1u << s;
       }
     }
     __syncwarp();
   }
 
-  // block: warps in order, float-float
+  // warp: lanes of equal q in float-float; lanes 0..Q-1 hold the warp sums
+  {
+    float2 v[NQ][CPL];
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+      v[0][c] = accN[c].ff();
+      v[1][c] = accD[c].ff();
+      if constexpr (HVP) {
+        v[2][c] = accCN[c].ff();
+        v[3][c] = accCD[c].ff();
+      }
+    }
+#pragma unroll
+    for (int off = Q; off < 32; off <<= 1)
+#pragma unroll
+      for (int qq = 0; qq < NQ; ++qq)
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) v[qq][c] = ff_add(v[qq][c], shfl_xor_ff(v[qq][c], off));
+    if (lane < Q)
+#pragma unroll
+      for (int qq = 0; qq < NQ; ++qq)
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) s_warp[wib][qq * K + c0 + c] = v[qq][c];
+  }
   __syncthreads();
   if (threadIdx.x < NV) {
     float2 acc = make_float2(0.f, 0.f);
-    for (int w = 0; w < kWarps; ++w)
-      acc = ff_add(acc, two_sum(s_acc[w][threadIdx.x][0], -s_acc[w][threadIdx.x][1]));
+    for (int w = 0; w < kWarps; ++w) acc = ff_add(acc, s_warp[w][threadIdx.x]);
     s_blk[threadIdx.x] = acc;
   }
   __syncthreads();

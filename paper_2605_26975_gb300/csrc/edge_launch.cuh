@@ -3,6 +3,7 @@
 #pragma once
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "edge_kernels.cuh"
 #include "internal.h"
@@ -14,22 +15,25 @@ pspec_status launch_edges_k(pspec_graph* g, const EdgeLaunch& L, cudaStream_t s)
   constexpr int Q = q_of(K);
   PSPEC_TRY(ensure_tasks(g, Q));
   const TaskSet& ts = g->tasks[Q == 1 ? 0 : Q == 2 ? 1 : 2];
+  constexpr size_t smem = edge_smem_bytes<Q>();
   static int occ = -1;
   if (occ < 0) {
-    PSPEC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, edge_kernel<K, HVP>, kBlock, 0));
+    PSPEC_CUDA(cudaFuncSetAttribute(edge_kernel<K, HVP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PSPEC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, edge_kernel<K, HVP>, kBlock, smem));
     occ = std::max(occ, 1);
+    if (const char* env = std::getenv("PSPEC_EDGE_BLOCKS_PER_SM")) occ = std::max(1, std::min(occ, std::atoi(env)));
   }
   EdgeArgs a;
-  a.rowptr = g->d_rowptr;
-  a.col = g->d_col;
-  a.val = g->d_val32;
+  a.rowptr = g->d_rowptr_s;
+  a.col = g->d_col_s;
+  a.val = g->d_val32_s;
+  a.perm = g->d_perm;
   a.U = L.U;
   a.V = L.V;
   a.out_a = L.out_a;
   a.out_b = L.out_b;
   a.tasks = ts.d_tasks;
   a.n_tasks = (int)ts.n_tasks;
-  a.chunk_edges = ts.chunk_edges;
   a.hub_part = g->d_hub_part;
   a.hub_first = ts.d_hub_first;
   a.hub_nchunk = ts.d_hub_nchunk;
@@ -46,7 +50,7 @@ pspec_status launch_edges_k(pspec_graph* g, const EdgeLaunch& L, cudaStream_t s)
   int blocks = grid_blocks(g, occ);
   blocks = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (ts.n_tasks + kWarps - 1) / kWarps));
   TimedScope timer(g, HVP ? "hvp_edges" : "eval_edges", s);
-  edge_kernel<K, HVP><<<blocks, kBlock, 0, s>>>(a);
+  edge_kernel<K, HVP><<<blocks, kBlock, smem, s>>>(a);
   PSPEC_CUDA(cudaGetLastError());
   return PSPEC_OK;
 }

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "edge_kernels.cuh"
 #include "internal.h"
 
 namespace pspec {
@@ -97,62 +98,62 @@ static int env_int(const char* name, int dflt) {
   return v ? std::atoi(v) : dflt;
 }
 
-// Build the warp-task partition for column split Q (see TaskSet).
+// Build the warp-task partition for column split Q (see TaskSet) over the
+// degree-sorted rows.  A row of degree d gets E edge slots, the smallest power
+// of two with d <= L*E (L = target edges per lane); a task takes up to
+// 32/(E*Q) consecutive sorted rows of the same E.  Rows longer than
+// hub_deg are split into chunks of chunk_edges entries.
 pspec_status ensure_tasks(pspec_graph* g, int Q) {
   int qi = Q == 1 ? 0 : Q == 2 ? 1 : 2;
   TaskSet& ts = g->tasks[qi];
   if (ts.built) return PSPEC_OK;
-  const int L = std::max(1, env_int("PSPEC_EDGES_PER_LANE", 8));
+  // at most edges_per_lane(Q) entries per lane: a task never exceeds
+  // task_max_entries(Q), the size of the kernels' shared-memory stages
+  const int L = std::max(1, std::min(edges_per_lane(Q), env_int("PSPEC_EDGES_PER_LANE", edges_per_lane(Q))));
   const int max_slots = 32 / Q;
   int max_elog = 0;
   while ((1 << max_elog) < max_slots) ++max_elog;
-  const int64_t hub_deg = (int64_t)L * max_slots * 4;
-  const int chunk = L * max_slots * 2;
-  const std::vector<int64_t>& rp = g->h_rowptr;
+  const int64_t hub_deg = (int64_t)L * max_slots;
+  const int chunk = L * max_slots;
+  const std::vector<int64_t>& rp = g->h_rowptr_s;
   const int64_t n = g->n;
   std::vector<int4> tasks;
   tasks.reserve((size_t)(n / 8 + 16));
   std::vector<int32_t> hub_row, hub_first, hub_nchunk, chunk_hub;
   int n_chunks = 0;
-  // graph boundaries (batched graphs: no task spans two graphs)
-  std::vector<int64_t> bounds = g->h_node_off;
-  if (bounds.empty()) bounds = {0, n};
-  size_t gi = 0;
+  auto elog_of = [&](int64_t d) {
+    int e = 0;
+    while (e < max_elog && d > (int64_t)L * (1 << e)) ++e;
+    return e;
+  };
+  // plain task: x = first sorted row, y = nrows | degree << 8 (all rows of a
+  // task have exactly this degree), z = elog, w = first entry of the task
   int64_t r = 0;
   while (r < n) {
-    while (bounds[gi + 1] <= r) ++gi;
-    const int64_t gend = bounds[gi + 1];
     const int64_t deg = rp[r + 1] - rp[r];
     if (deg > hub_deg) {
       int nch = (int)((deg + chunk - 1) / chunk);
       hub_row.push_back((int32_t)r);
       hub_first.push_back(n_chunks);
       hub_nchunk.push_back(nch);
+      // hub chunk: x = sorted row, y = chunk slot, z = elog | hub | first | len << 10,
+      // w = first entry of the chunk
       for (int c = 0; c < nch; ++c) {
-        tasks.push_back(make_int4((int)r, c, max_elog | (1 << 8), n_chunks + c));
+        const int64_t len = std::min<int64_t>(chunk, deg - (int64_t)c * chunk);
+        tasks.push_back(make_int4((int)r, n_chunks + c,
+                                  max_elog | (1 << 8) | ((c == 0 ? 1 : 0) << 9) | (int)(len << 10),
+                                  (int)(rp[r] + (int64_t)c * chunk)));
         chunk_hub.push_back((int32_t)hub_row.size() - 1);
       }
       n_chunks += nch;
       ++r;
       continue;
     }
-    int elog = 0, nrows = 1;
-    for (elog = 0; elog <= max_elog; ++elog) {
-      const int E = 1 << elog;
-      const int R = 32 / (E * Q);
-      int64_t maxdeg = 0;
-      int cnt = 0;
-      for (int64_t i = r; i < std::min(gend, r + R); ++i) {
-        int64_t d = rp[i + 1] - rp[i];
-        if (d > hub_deg) break;
-        maxdeg = std::max(maxdeg, d);
-        ++cnt;
-      }
-      nrows = std::max(cnt, 1);
-      if (maxdeg <= (int64_t)L * E || elog == max_elog) break;
-    }
-    if (elog > max_elog) elog = max_elog;
-    tasks.push_back(make_int4((int)r, nrows, elog, 0));
+    const int elog = elog_of(deg);
+    const int R = 32 / ((1 << elog) * Q);
+    int nrows = 0;
+    while (nrows < R && r + nrows < n && rp[r + nrows + 1] - rp[r + nrows] == deg) ++nrows;
+    tasks.push_back(make_int4((int)r, nrows | (int)(deg << 8), elog, (int)rp[r]));
     r += nrows;
   }
   ts.Q = Q;
@@ -341,6 +342,43 @@ static pspec_status create_impl(int64_t n, const int64_t* rowptr_in, const int32
   if (!node_off.empty())
     if ((st = copy(g->d_node_off, node_off.data(), sizeof(int64_t) * node_off.size())) != PSPEC_OK)
       return fail(st);
+  // rows stably sorted by degree: the fast kernels' layout
+  {
+    std::vector<int32_t> perm(n);
+    for (int64_t i = 0; i < n; ++i) perm[i] = (int32_t)i;
+    const std::vector<int64_t>& rp0 = g->h_rowptr;
+    std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) {
+      return rp0[a + 1] - rp0[a] < rp0[b + 1] - rp0[b];
+    });
+    std::vector<int64_t> rps(n + 1, 0);
+    for (int64_t r = 0; r < n; ++r) rps[r + 1] = rps[r] + (rp0[perm[r] + 1] - rp0[perm[r]]);
+    std::vector<int32_t> cs(nnz);
+    std::vector<float> vs(nnz);
+    for (int64_t r = 0; r < n; ++r) {
+      const int64_t src = rp0[perm[r]], len = rps[r + 1] - rps[r];
+      std::copy(col.begin() + src, col.begin() + src + len, cs.begin() + rps[r]);
+      std::copy(v32.begin() + src, v32.begin() + src + len, vs.begin() + rps[r]);
+    }
+    auto alloc = [&](void** p, size_t bytes) {
+      cudaError_t e = cudaMalloc(p, bytes);
+      return e == cudaSuccess ? PSPEC_OK : cuda_error(e, "cudaMalloc(sorted CSR)");
+    };
+    if ((st = alloc((void**)&g->d_rowptr_s, sizeof(int64_t) * (n + 1))) != PSPEC_OK) return fail(st);
+    // padded by 64 bytes: the edge kernels prefetch 16-byte-rounded windows
+    if ((st = alloc((void**)&g->d_col_s, sizeof(int32_t) * (nnz + 16))) != PSPEC_OK) return fail(st);
+    if ((st = alloc((void**)&g->d_val32_s, sizeof(float) * (nnz + 16))) != PSPEC_OK) return fail(st);
+    if ((st = alloc((void**)&g->d_perm, sizeof(int32_t) * (n + 16))) != PSPEC_OK) return fail(st);
+    if ((st = copy(g->d_rowptr_s, rps.data(), sizeof(int64_t) * (n + 1))) != PSPEC_OK) return fail(st);
+    if ((st = copy(g->d_perm, perm.data(), sizeof(int32_t) * n)) != PSPEC_OK) return fail(st);
+    if (nnz) {
+      if ((st = copy(g->d_col_s, cs.data(), sizeof(int32_t) * nnz)) != PSPEC_OK) return fail(st);
+      if ((st = copy(g->d_val32_s, vs.data(), sizeof(float) * nnz)) != PSPEC_OK) return fail(st);
+    }
+    cudaError_t e2 = cudaStreamSynchronize(s);  // the host vectors go out of scope
+    if (e2 != cudaSuccess) return fail(cuda_error(e2, "sorted CSR upload"));
+    g->h_rowptr_s = std::move(rps);
+    g->h_perm = std::move(perm);
+  }
   cudaMemsetAsync(g->d_counters, 0, sizeof(unsigned) * (max_groups + 8), s);
   cudaMemsetAsync(g->d_status, 0, sizeof(int), s);
   cudaMemsetAsync(g->d_scalars, 0, sizeof(double) * 1024, s);
@@ -387,6 +425,10 @@ void pspec_graph_destroy(pspec_graph* g) {
   }
   cudaFree(g->d_rowptr);
   cudaFree(g->d_col);
+  cudaFree(g->d_rowptr_s);
+  cudaFree(g->d_col_s);
+  cudaFree(g->d_val32_s);
+  cudaFree(g->d_perm);
   cudaFree(g->d_val32);
   cudaFree(g->d_val64);
   cudaFree(g->d_node_off);

@@ -14,9 +14,10 @@
 namespace pspec {
 
 // ------------------------------------------------------------ row tasks ---
-// The edge kernels walk a list of warp tasks.  A plain task covers `nrows`
-// consecutive rows starting at `row`, each row processed by a team of
-// E = 2^elog edge slots x Q column lanes (E*Q*nrows <= 32).  A hub chunk task
+// The edge kernels walk a list of warp tasks over the degree-sorted rows.  A
+// plain task covers `nrows` consecutive sorted rows starting at `row`, each
+// processed by a team of E = 2^elog edge slots x Q column lanes
+// (E*Q*nrows <= 32); sorting makes the rows of a task (nearly) equally long.  A hub chunk task
 // covers edges [rowptr[row] + chunk*chunk_edges, ...) of one long row with the
 // whole warp; its partial row sums go to hub slot `slot`, and the warp that
 // finishes the row's last chunk adds the chunks up in chunk order.
@@ -53,12 +54,20 @@ struct pspec_graph {
   int32_t n_graphs = 1;
   int device = 0;
   int sm_count = 0;
-  // device CSR
+  // device CSR in the caller's row order
   int64_t* d_rowptr = nullptr;
   int32_t* d_col = nullptr;
   float* d_val32 = nullptr;
   double* d_val64 = nullptr;
   std::vector<int64_t> h_rowptr;     // host copy (task building, batching)
+  // the same matrix with its rows stably sorted by degree (fast edge kernels):
+  // sorted row r is row d_perm[r] of W; column indices are unchanged
+  int64_t* d_rowptr_s = nullptr;
+  int32_t* d_col_s = nullptr;
+  float* d_val32_s = nullptr;
+  int32_t* d_perm = nullptr;
+  std::vector<int64_t> h_rowptr_s;
+  std::vector<int32_t> h_perm;
   // batched graphs
   std::vector<int64_t> h_node_off;
   int64_t* d_node_off = nullptr;
