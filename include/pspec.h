@@ -140,6 +140,29 @@ pspec_status pspec_eval(pspec_graph* g, const void* U, int k, double p, pspec_dt
 pspec_status pspec_hvp(pspec_graph* g, const void* U, const void* V, int k, double p,
                        pspec_dtype dtype, void* HV_out, unsigned flags, void* stream);
 
+/* ------------------------------------------------------ hvp, no allocation ---
+ * pspec_hvp_noalloc: the same Hessian-vector product as pspec_hvp (FP32,
+ * device pointers), for callers that must not allocate device memory: code
+ * that runs where cudaMalloc is forbidden or unsafe (a host callback on a
+ * stream, a section that must not synchronise the device, an allocator
+ * owned by another runtime) or that cannot create a graph handle.  The paper
+ * has no counterpart; this is an interface convenience.
+ *   rowptr/col/val: W in CSR (both triangles, FP32 weights), device memory
+ *   U, V, HV_out:   n x k row-major FP32, device memory, HV_out not aliasing
+ * Working memory (the rows of Delta_p u and the reduction partials) is one
+ * fixed array in the library's device globals, about 2.6 MB, held on every
+ * GPU that loads the library until the process exits; hence the limit
+ * n * k <= 524288 (INVALID_ARG beyond it, with a message).  The arguments
+ * are not validated on the device (col must lie in [0, n), weights >= 0).
+ * The first call on a device, with that device current, looks up the
+ * array's device address; make that first call before any stream capture.
+ * Every call uses the same array: calls whose work overlaps on the GPU
+ * (other streams, other host threads) race and give wrong results.  Errors:
+ * INVALID_ARG, CUDA.  Enqueued on `stream`; does not synchronise. */
+pspec_status pspec_hvp_noalloc(int64_t n, const int64_t* rowptr, const int32_t* col,
+                               const float* val, const float* U, const float* V, int k, double p,
+                               float* HV_out, void* stream);
+
 /* ---------------------------------------------------------------- solve ---
  * pspec_solve: minimise Eq. 1 "for progressively smaller values of p"
  * (Section 2): for each p of p_schedule (each in (1,2], non-increasing), a

@@ -60,6 +60,8 @@ _SIGS = {
     "pspec_kmeans": (C.c_int, [_vp, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_int,
                                C.c_int, _vp, _vp, C.POINTER(C.c_double), _vp]),
     "pspec_rcut": (C.c_int, [_vp, _vp, C.c_int, C.POINTER(C.c_double), _vp]),
+    "pspec_hvp_noalloc": (C.c_int, [C.c_int64, _vp, _vp, _vp, _vp, _vp, C.c_int, C.c_double, _vp,
+                                    _vp]),
     "pspec_set_timing": (C.c_int, [_vp, C.c_int]),
     "pspec_kernel_times": (C.c_int, [_vp, C.c_char_p, C.c_size_t]),
     "pspec_last_error": (C.c_char_p, []),
