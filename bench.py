@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--eager", action="store_true", help="launch the step's kernels one by one")
     return ap.parse_args()
 
 
@@ -295,6 +296,18 @@ def main():
         step()
     torch.cuda.synchronize()
     assert G.status() == 0
+    # the step (eval + hvp: 4 kernel launches) replayed as one CUDA graph, so
+    # host launch latency does not sit between the kernels
+    graph = None
+    if not args.eager:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        graph.replay()
+        torch.cuda.synchronize()
+        run_step = graph.replay
+    else:
+        run_step = step
 
     # ---- timed region: device time of every step, L2 flushed before each
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -308,7 +321,7 @@ def main():
     for i in range(args.steps):
         flush.zero_()
         starts[i].record(stream)
-        step()
+        run_step()
         ends[i].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
@@ -395,7 +408,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": describe(args.workload, g, k), "p": P_BENCH,
-                       "step": "pspec_eval (F + grad) + pspec_hvp",
+                       "step": "pspec_eval (F + grad) + pspec_hvp" + ("" if args.eager else ", replayed as a CUDA graph"),
                        "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
