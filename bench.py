@@ -47,9 +47,11 @@ KERNEL_SOURCES = ["paper_2605_26975_gb300/csrc/edge_kernels.cuh",
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: enough for about 2 s of timed region, at least 50)")
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="knn_gmm", choices=["knn_gmm", "grid3d", "dcsbm", "sbm4"])
+    ap.add_argument("--workload", default="knn_gmm",
+                    choices=["knn_gmm", "grid3d", "dcsbm", "sbm4", "sbm_batch"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -57,14 +59,53 @@ def parse():
     return ap.parse_args()
 
 
-def describe(name, g, k):
+def describe(name, n, nnz, k):
     desc = {
         "knn_gmm": "kNN similarity graph: 200,000 points, 8 isotropic 2-D Gaussians, 10-NN symmetrised, w=exp(-d^2/0.25)",
         "grid3d": "3-D 200^3 6-neighbour grid, w~U[0.5,1.5], 0.1% long-range links",
         "dcsbm": "degree-corrected SBM, n=1,000,000, 16 blocks, Pareto(2.5) degrees, w~U[0.1,1]",
         "sbm4": "SBM n=1,000, 4 blocks, p_in 0.05, p_out 0.002",
+        "sbm_batch": "512 SBMs, n log-uniform in [500, 50,000], 2..8 blocks, mean degree 8..20, "
+                     "k in {2,4,8}; one batched handle per k",
     }[name]
-    return f"{desc} (n={g.n}, nnz={g.nnz}, k={k})"
+    return f"{desc} (n={n}, nnz={nnz}, k={k})"
+
+
+class Part:
+    """One graph handle of the workload: its CSR (a batch's concatenation for
+    sbm_batch), vertex offsets of the graphs in it, and the blocks U, V."""
+
+    def __init__(self, csr, node_off, graphs, U, V, k):
+        self.csr, self.node_off, self.graphs, self.U, self.V, self.k = csr, node_off, graphs, U, V, k
+
+    def edge_cols(self):
+        return 2 * self.csr.nnz * self.k
+
+    def samples(self):
+        """(graph, U rows, V rows) of every graph in the part."""
+        if self.node_off is None:
+            return [(self.csr, self.U, self.V)]
+        o = self.node_off
+        return [(g, self.U[o[i]:o[i + 1]], self.V[o[i]:o[i + 1]]) for i, g in enumerate(self.graphs)]
+
+
+def build_parts(name, rank=0):
+    """The workload as a list of Parts; sbm_batch is grouped by k (a handle
+    holds graphs of one k), every other workload is one graph."""
+    info = wl.WORKLOADS[name]
+    if name == "sbm_batch":
+        gs, us, vs = replica_seeds(name, rank)
+        batch = wl.make_graph(name) if rank == 0 else wl.sbm_batch(gs)
+        parts = []
+        for k in (2, 4, 8):
+            idx = np.flatnonzero(batch.k == k)
+            sub = wl.concat_graphs([batch.graphs[i] for i in idx], [k] * idx.size)
+            n = sub.csr.n
+            parts.append(Part(sub.csr, sub.node_off, sub.graphs, wl.orthonormal_block(us + 10 * k, n, k),
+                              wl.gaussian_block(vs + 10 * k, n, k), k))
+        return parts, info
+    g, U, V, info = build_workload(name, seed_shift=rank)
+    return [Part(g, None, None, U, V, info["k"])], info
 
 
 def bytes_eval_edges(g, k):
@@ -135,19 +176,33 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def wait_ready(self, timeout=10.0):
+        """Block until the first sample arrives (nvidia-smi takes a moment to start)."""
+        t0 = time.perf_counter()
+        while self.proc is not None and not self.lines and time.perf_counter() - t0 < timeout:
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
-            return None
+            return
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+
+    def summary(self, t0, t1):
+        """Median SM clock, max clock and active throttle reasons of the samples
+        that arrived between host times t0 and t1."""
+        if self.proc is None:
+            return None
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ts, ln in self.lines:
+            if not t0 <= ts <= t1:
+                continue
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 8:
                 continue
@@ -160,7 +215,7 @@ class ClockSampler:
                 if v.lower().startswith("active"):
                     reasons.add(name)
         if not sm:
-            return None
+            return {"sm_mhz": None, "sm_max_mhz": None, "samples": 0, "reasons": []}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
                 "reasons": sorted(reasons)}
 
@@ -197,6 +252,13 @@ def replica_seeds(name, rank):
     return 1000 + idx + 100 * rank, 2000 + idx + 100 * rank, 3000 + idx + 100 * rank
 
 
+def workload_desc(name, parts):
+    n = sum(pt.csr.n for pt in parts)
+    nnz = sum(pt.csr.nnz for pt in parts)
+    ks = "/".join(str(pt.k) for pt in parts)
+    return describe(name, n, nnz, ks)
+
+
 def build_workload(name, seed_shift=0):
     info = wl.WORKLOADS[name]
     if seed_shift == 0:
@@ -213,51 +275,57 @@ def build_workload(name, seed_shift=0):
     return g, U, V, info
 
 
-def cpu_baseline(g, U, V, p, k, budget_s=12.0):
-    """The oracle as it stands (numpy FP64, one thread) on a bounded sample:
-    full eval+HVP steps on the same graph until ~budget_s seconds pass."""
+def oracle_steps(parts, p, budget_s, max_steps):
+    """The oracle as it stands (numpy FP64, one thread): eval+grad+HVP on the
+    workload's graphs in order (cycling) until budget_s seconds or max_steps
+    graph-steps pass.  Returns (edge-columns done, seconds, graph-steps)."""
     import oracle
-    U64, V64 = U.astype(np.float64), V.astype(np.float64)
+    items = [(g, U.astype(np.float64), V.astype(np.float64), part.k)
+             for part in parts for g, U, V in part.samples()]
     t0 = time.perf_counter()
-    steps = 0
+    done = steps = 0
     while True:
+        g, U64, V64, k = items[steps % len(items)]
         oracle.objective(g, U64, p)
         oracle.euclidean_grad(g, U64, p)
         oracle.euclidean_hvp(g, U64, V64, p)
+        done += 2 * g.nnz * k
         steps += 1
-        if time.perf_counter() - t0 > budget_s or steps >= 20:
+        if time.perf_counter() - t0 > budget_s or steps >= max_steps:
             break
-    dt = time.perf_counter() - t0
-    return {"value": 2 * g.nnz * k * steps / dt, "unit": "edge*col/s", "cores": 1, "kind": "oracle",
-            "sample": f"{steps} full eval+grad+HVP step(s) of the FP64 numpy oracle on this workload "
+    return done, time.perf_counter() - t0, steps
+
+
+def cpu_baseline(parts, p, budget_s=12.0):
+    """The oracle on a bounded sample of the workload (~budget_s seconds)."""
+    max_steps = 20 if len(parts) == 1 else 10_000
+    done, dt, steps = oracle_steps(parts, p, budget_s, max_steps)
+    what = "full eval+grad+HVP step(s)" if len(parts) == 1 else "graphs' eval+grad+HVP steps"
+    return {"value": done / dt, "unit": "edge*col/s", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} {what} of the FP64 numpy oracle on this workload "
                       f"({dt:.1f} s, single-threaded numpy)"}
 
 
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
-    g, U, V, info = build_workload(args.workload)
-    k = info["k"]
-    # each timed step is one oracle eval+HVP; keep the run to a few minutes
-    import oracle
-    U64, V64 = U.astype(np.float64), V.astype(np.float64)
-    for _ in range(min(args.warmup, 1)):
-        oracle.euclidean_grad(g, U64, P_BENCH)
+    parts, info = build_parts(args.workload)
+    # each timed step is one oracle eval+grad+HVP of the workload's graph (of
+    # up to 40 of a batch's graphs); keep the run to a few minutes
     steps = max(1, min(args.steps, 5))
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        oracle.objective(g, U64, P_BENCH)
-        oracle.euclidean_grad(g, U64, P_BENCH)
-        oracle.euclidean_hvp(g, U64, V64, P_BENCH)
-    dt = time.perf_counter() - t0
-    value = 2 * g.nnz * k * steps / dt
+    per_step = 1 if len(parts) == 1 else 40
+    oracle_steps(parts, P_BENCH, 0.0, 1)  # warm-up
+    done, dt, _ = oracle_steps(parts, P_BENCH, float("inf"), steps * per_step)
+    value = done / dt
     line = {"impl": "reference", "metric": "p-Laplacian grad+HVP throughput",
             "value": value, "unit": "edge*col/s", "n_gpus": args.gpus, "steps": steps,
-            "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * dt / steps,
+            "warmup": 1, "ms_per_step": 1e3 * dt / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": describe(args.workload, g, k), "p": P_BENCH},
+            "data": "synthetic", "config": {"workload": workload_desc(args.workload, parts),
+                                            "p": P_BENCH},
             "cpu_baseline": {"value": value, "unit": "edge*col/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{steps} eval+grad+HVP step(s) of the FP64 numpy oracle"},
+                             "sample": f"{steps} step(s) of {per_step} graph eval+grad+HVP of the "
+                                       f"FP64 numpy oracle"},
             "e2e": {"value": value, "unit": "edge*col/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -278,26 +346,37 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    g, U, V, info = build_workload(args.workload, seed_shift=rank)
-    k = info["k"]
-    G = api.Graph.from_csr(g)
-    Ud = torch.from_numpy(U).cuda()
-    Vd = torch.from_numpy(V).cuda()
-    grad = torch.empty_like(Ud)
-    HV = torch.empty_like(Ud)
+    parts, info = build_parts(args.workload, rank)
+    for pt in parts:
+        pt.G = api.Graph(pt.csr.rowptr, pt.csr.col, pt.csr.val, node_off=pt.node_off)
+        pt.Ud = torch.from_numpy(pt.U).cuda()
+        pt.Vd = torch.from_numpy(pt.V).cuda()
+        pt.grad = torch.empty_like(pt.Ud)
+        pt.HV = torch.empty_like(pt.Ud)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
     def step():
-        G.eval(Ud, P_BENCH, grad_out=grad)
-        G.hvp(Ud, Vd, P_BENCH, out=HV)
+        for pt in parts:
+            pt.G.eval(pt.Ud, P_BENCH, grad_out=pt.grad)
+            pt.G.hvp(pt.Ud, pt.Vd, P_BENCH, out=pt.HV)
 
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
-    assert G.status() == 0
-    # the step (eval + hvp: 4 kernel launches) replayed as one CUDA graph, so
-    # host launch latency does not sit between the kernels
+    for pt in parts:
+        assert pt.G.status() == 0
+    if args.steps is None:  # about 2 s of timed region, from one timed warm-up step
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        flush.zero_()
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        args.steps = int(min(20000, max(50, 2000.0 / max(e0.elapsed_time(e1), 1e-3))))
+    # the step (per handle eval + hvp: 4 kernel launches, 6 for a batch)
+    # replayed as one CUDA graph, so host launch latency does not sit between
+    # the kernels
     graph = None
     if not args.eager:
         graph = torch.cuda.CUDAGraph()
@@ -314,6 +393,7 @@ def main():
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     sampler = ClockSampler(local)
     sampler.start()
+    sampler.wait_ready()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -324,71 +404,98 @@ def main():
         run_step()
         ends[i].record(stream)
     torch.cuda.synchronize()
-    wall = time.perf_counter() - wall0
+    wall1 = time.perf_counter()
+    wall = wall1 - wall0
     if world > 1:
         dist.barrier()
-    clocks = sampler.stop()
+    clocks = sampler.summary(wall0, wall1)
+    if clocks is not None and clocks["samples"] == 0:
+        # a region shorter than the sampling period: keep the GPU under the same
+        # step loop for one more second and report the samples of both
+        while time.perf_counter() - wall1 < 1.0:
+            for _ in range(20):
+                flush.zero_()
+                run_step()
+            torch.cuda.synchronize()
+        clocks = sampler.summary(wall0, time.perf_counter())
+        if clocks is not None:
+            clocks["window"] = "timed region + 1 s of the same step loop right after it"
+    sampler.stop()
     ms_local = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps
-    edge_cols = 2 * g.nnz * k
+    edge_cols = sum(pt.edge_cols() for pt in parts)
     value, ms = job_throughput(ms_local, edge_cols, dist if world > 1 else None)
 
     # ---- per-kernel device times (same steps, library events on the stream)
-    G.set_timing(True)
+    for pt in parts:
+        pt.G.set_timing(True)
     for _ in range(args.steps):
         flush.zero_()
         step()
     torch.cuda.synchronize()
-    times = G.kernel_times()
-    G.set_timing(False)
+    times = {}
+    for pt in parts:
+        for name, (c, t) in pt.G.kernel_times().items():
+            c0, t0 = times.get(name, (0, 0.0))
+            times[name] = (c0 + c, t0 + t)
+        pt.G.set_timing(False)
     launches = sum(c for c, _ in times.values()) // args.steps
     shares = {name: t for name, (c, t) in times.items()}
     dom = max(shares, key=shares.get)
     dom_launches, dom_ms = times[dom]
-    algo = {"hvp_edges": bytes_hvp_edges(g, k), "eval_edges": bytes_eval_edges(g, k)}.get(dom)
+    byte_fn = {"hvp_edges": bytes_hvp_edges, "eval_edges": bytes_eval_edges}.get(dom)
     peak, peak_kind = measured_peak()
     roofline = None
-    if algo is not None:
-        achieved = algo / (dom_ms / dom_launches * 1e-3) / 1e9
+    if byte_fn is not None:
+        algo_step = sum(byte_fn(pt.csr, pt.k) for pt in parts)  # one launch per handle
+        achieved = algo_step * args.steps / (dom_ms * 1e-3) / 1e9
         roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
                     "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
-                    "traffic": read_traffic(dom, args.workload),
-                    "algorithmic_bytes_per_launch": algo,
+                    "traffic": read_traffic(dom, args.workload) if len(parts) == 1 else None,
+                    "algorithmic_bytes_per_launch": algo_step / len(parts),
+                    "launches_per_step": len(parts),
                     "mean_launch_ms": dom_ms / dom_launches,
                     "kernel_ms_per_step": {n: t / args.steps for n, (c, t) in times.items()}}
 
     # ---- e2e through the C ABI with pinned host buffers
-    Uh = torch.from_numpy(U).pin_memory()
-    Vh = torch.from_numpy(V).pin_memory()
-    gh = torch.empty_like(Uh).pin_memory()
-    hh = torch.empty_like(Uh).pin_memory()
+    for pt in parts:
+        pt.Uh = torch.from_numpy(pt.U).pin_memory()
+        pt.Vh = torch.from_numpy(pt.V).pin_memory()
+        pt.gh = torch.empty_like(pt.Uh).pin_memory()
+        pt.hh = torch.empty_like(pt.Uh).pin_memory()
+
+    def host_step():
+        for pt in parts:
+            pt.G.eval_host(pt.Uh, P_BENCH, pt.gh)
+            pt.G.hvp_host(pt.Uh, pt.Vh, P_BENCH, pt.hh)
+
     for _ in range(2):
-        G.eval_host(Uh, P_BENCH, gh)
-        G.hvp_host(Uh, Vh, P_BENCH, hh)
-    e2e_steps = max(3, args.steps // 2)
+        host_step()
+    e2e_steps = max(3, min(args.steps // 2, 100))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         flush.zero_()
-        G.eval_host(Uh, P_BENCH, gh)
-        G.hvp_host(Uh, Vh, P_BENCH, hh)
+        host_step()
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    blk = g.n * k * 4
+    blk = sum(pt.csr.n * pt.k * 4 for pt in parts)
+    n_f = sum(pt.G.n_graphs for pt in parts)
     e2e = {"value": world * edge_cols / e2e_s, "unit": "edge*col/s",
-           "h2d_bytes_per_step": 3 * blk, "d2h_bytes_per_step": 2 * blk + 8,
+           "h2d_bytes_per_step": 3 * blk, "d2h_bytes_per_step": 2 * blk + 8 * n_f,
            "note": "wall clock per step incl. a 256 MB L2 flush; copies and kernels synchronous"}
 
     # ---- full solve to the last p, FP32 fast path vs plain FP64 path
     solve = None
-    if not args.no_solve and rank == 0:
+    if not args.no_solve and rank == 0 and len(parts) == 1:
+        pt = parts[0]
         sched = list(info["p_schedule"])
         opts = api.default_opts()
         t0 = time.perf_counter()
-        _, lab32, rc32, st32, s32 = G.solve(Ud, sched, opts)
+        _, lab32, rc32, st32, s32 = pt.G.solve(pt.Ud, sched, opts)
         t32 = time.perf_counter() - t0
-        U64 = torch.from_numpy(U.astype(np.float64)).cuda()
+        U64 = torch.from_numpy(pt.U.astype(np.float64)).cuda()
         t0 = time.perf_counter()
-        _, lab64, rc64, st64, s64 = G.solve(U64, sched, opts)
+        _, lab64, rc64, st64, s64 = pt.G.solve(U64, sched, opts)
         t64 = time.perf_counter() - t0
         solve = {"p_schedule": sched, "fast_f32_s": t32, "plain_f64_s": t64,
                  "speedup": t64 / t32, "rcut_f32": rc32, "rcut_f64": rc64,
@@ -398,7 +505,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cpu = cpu_baseline(g, U, V, P_BENCH, k)
+        cpu = cpu_baseline(parts, P_BENCH)
 
     if rank == 0:
         line = {
@@ -407,8 +514,9 @@ def main():
             "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": describe(args.workload, g, k), "p": P_BENCH,
-                       "step": "pspec_eval (F + grad) + pspec_hvp" + ("" if args.eager else ", replayed as a CUDA graph"),
+            "config": {"workload": workload_desc(args.workload, parts), "p": P_BENCH,
+                       "step": "pspec_eval (F + grad) + pspec_hvp" + (" per handle" if len(parts) > 1 else "")
+                               + ("" if args.eager else ", replayed as a CUDA graph"),
                        "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,

@@ -118,10 +118,11 @@ pspec_status pspec_graph_status(pspec_graph* g, void* stream);
  *   parts_out  = optional (NULL to skip) FP64[2k]: N_0..N_{k-1}, D_0..D_{k-1}
  * U and grad_out have type `dtype`; grad_out may not alias U.  F_out and
  * parts_out are device pointers (host with PSPEC_HOST_PTRS).  On a batched
- * graph F_out and parts_out hold one entry per graph (F_out[G],
- * parts_out[G][2k]) and k is the row stride shared by all graphs.
- * Errors: INVALID_ARG (k, p, NULL, misalignment), CUDA; ZERO_COLUMN and
- * NONFINITE through the status word. */
+ * graph every graph has k columns (group graphs of different k into
+ * separate handles), F_out holds G values and parts_out G x 2k (graph g's
+ * N then D at [g*2k]); the call runs the FP32 path only (dtype F32, else
+ * INVALID_ARG).  Errors: INVALID_ARG (k, p, NULL, misalignment), CUDA;
+ * ZERO_COLUMN and NONFINITE through the status word. */
 pspec_status pspec_eval(pspec_graph* g, const void* U, int k, double p, pspec_dtype dtype,
                         double* F_out, void* grad_out, double* parts_out, unsigned flags,
                         void* stream);
@@ -136,7 +137,8 @@ pspec_status pspec_eval(pspec_graph* g, const void* U, int k, double p, pspec_dt
  * A zero difference d_aj == 0 (or u_a == 0) contributes no curvature term.
  * The sparse-plus-diagonal part is what Algorithm 1 applies column by
  * column; the rank-two terms complete the Hessian of the quotient.
- * HV_out may not alias U or V.  Errors as pspec_eval. */
+ * On a batched graph lambda, D, g_N and g_D are each graph's own (FP32
+ * only, as pspec_eval).  HV_out may not alias U or V.  Errors as pspec_eval. */
 pspec_status pspec_hvp(pspec_graph* g, const void* U, const void* V, int k, double p,
                        pspec_dtype dtype, void* HV_out, unsigned flags, void* stream);
 
@@ -233,7 +235,8 @@ pspec_status pspec_kmeans(const void* X, int64_t n, int dim, pspec_dtype dtype, 
  * pspec_rcut: RCut(C_1..C_c) = sum_c cut(C_c, complement)/|C_c| (Section
  * 3.1) with cut(C, C') = sum over i in C, j in C' of w_ij; empty clusters
  * contribute nothing.  labels device int32[n] in [0, n_clusters).
- * rcut_out host double.  Synchronises `stream`. */
+ * rcut_out host double.  Synchronises `stream`.  INVALID_ARG on a batched
+ * handle (one RCut per graph: call it on each graph's own handle). */
 pspec_status pspec_rcut(pspec_graph* g, const int32_t* labels, int n_clusters, double* rcut_out,
                         void* stream);
 

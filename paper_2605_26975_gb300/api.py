@@ -85,12 +85,14 @@ class Graph:
 
     # ------------------------------------------------------------ per call
     def eval(self, U, p, grad_out=None, parts=False):
-        """(F, grad[, parts]) with F a 1-element float64 CUDA tensor."""
+        """(F, grad[, parts]): F a float64 CUDA tensor with one entry per graph
+        of the handle, parts [n_graphs * 2k] (each graph's N_1..N_k, D_1..D_k)."""
         U = _dev_block(U, "U", self.n)
         k = U.shape[1]
+        G = self.n_graphs
         grad = torch.empty_like(U) if grad_out is None else grad_out
-        F = torch.empty(1, dtype=torch.float64, device=U.device)
-        P = torch.empty(2 * k, dtype=torch.float64, device=U.device) if parts else None
+        F = torch.empty(G, dtype=torch.float64, device=U.device)
+        P = torch.empty(G * 2 * k, dtype=torch.float64, device=U.device) if parts else None
         st = lib().pspec_eval(self._h, _ptr(U), k, float(p), _DT[U.dtype], _ptr(F), _ptr(grad),
                               _ptr(P), 0, _stream())
         check(st, "pspec_eval")
@@ -109,14 +111,15 @@ class Graph:
 
     def eval_host(self, U, p, grad_out):
         """pspec_eval with PSPEC_HOST_PTRS: U and grad_out are CPU tensors
-        (pinned for asynchronous copies); returns F as a Python float."""
+        (pinned for asynchronous copies); returns F as a Python float (a list
+        of floats, one per graph, for a batched handle)."""
         k = U.shape[1]
-        F = C.c_double()
+        F = (C.c_double * self.n_graphs)()
         st = lib().pspec_eval(self._h, C.c_void_p(U.data_ptr()), k, float(p), _DT[U.dtype],
-                              C.byref(F), C.c_void_p(grad_out.data_ptr()), None,
+                              F, C.c_void_p(grad_out.data_ptr()), None,
                               _abi.PSPEC_HOST_PTRS, _stream())
         check(st, "pspec_eval(host)")
-        return F.value
+        return F[0] if self.n_graphs == 1 else list(F)
 
     def hvp_host(self, U, V, p, out):
         st = lib().pspec_hvp(self._h, C.c_void_p(U.data_ptr()), C.c_void_p(V.data_ptr()),

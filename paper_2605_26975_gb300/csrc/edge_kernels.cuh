@@ -45,7 +45,7 @@ namespace pspec {
 __host__ __device__ constexpr int edges_per_lane(int Q) { return 8 * Q; }
 __host__ __device__ constexpr int task_max_entries(int Q) { return 32 * edges_per_lane(Q) / Q; }
 constexpr int kStages = 3;
-constexpr uint32_t kWaitTries = 1u << 20;
+constexpr uint32_t kWaitTries = 2000;  // x up to 1 ms each: about 2 s before a timeout
 
 template <int Q>
 struct StageBuf {
@@ -83,6 +83,9 @@ struct EdgeArgs {
   double* scalars;
   int* status;
   const int* skip;
+  // batches: per-task column sums go to task_part[task][NV] instead of the
+  // grid reduction (NULL for a single graph)
+  float* task_part;
 };
 
 template <int K, int CPL, int VW>
@@ -288,30 +291,76 @@ __global__ void __launch_bounds__(kBlock) edge_kernel(EdgeArgs a) {
     }
     const bool lead = active && slot == 0;
     const bool first_chunk = !hub || ((task.z >> 9) & 1);
+    // this task's contributions of this lane to the per-column sums
+    float tN[CPL], tD[CPL], tCN[CPL], tCD[CPL];
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) { tN[c] = 0.f; tD[c] = 0.f; tCN[c] = 0.f; tCD[c] = 0.f; }
     if (lead) {
 #pragma unroll
-      for (int c = 0; c < CPL; ++c) accN[c].add(nsum[c]);
+      for (int c = 0; c < CPL; ++c) tN[c] = nsum[c];
       if (first_chunk) {  // vertex terms once per row
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
           const float phu = abs_pow_pm2_clamped(ui[c], pm2) * ui[c];  // phi_p(u_i)
-          accD[c].add(phu * ui[c]);                                   // |u_i|^p
-          if constexpr (HVP) accCD[c].add(phu * vi[c]);
+          tD[c] = phu * ui[c];                                        // |u_i|^p
+          if constexpr (HVP) tCD[c] = phu * vi[c];
         }
       }
+      // sigma_N: a whole row's Delta_i v_i, or a chunk's share of it
+#pragma unroll
+      for (int c = 0; c < CPL; ++c)
+        if constexpr (HVP) tCN[c] = dsum[c] * vi[c];
       if (!hub) {
         if constexpr (HVP) {
           store_row<K, CPL, VW>(a.out_a, row, c0, ssum);
           store_row<K, CPL, VW>(a.out_b, row, c0, dsum);
-#pragma unroll
-          for (int c = 0; c < CPL; ++c) accCN[c].add(dsum[c] * vi[c]);
         } else {
           store_row<K, CPL, VW>(a.out_a, row, c0, dsum);
         }
       }
     }
+    if (!a.task_part) {
+      if (lead) {
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+          accN[c].add(tN[c]);
+          accD[c].add(tD[c]);
+          if constexpr (HVP) {
+            accCN[c].add(tCN[c]);
+            accCD[c].add(tCD[c]);
+          }
+        }
+      }
+    } else {
+      // one graph of a batch: fold the task's sums over the warp (lanes of
+      // equal q) and publish them in the task's slot
+      for (int off = Q; off < 32; off <<= 1)
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+          tN[c] += __shfl_xor_sync(0xffffffffu, tN[c], off);
+          tD[c] += __shfl_xor_sync(0xffffffffu, tD[c], off);
+          if constexpr (HVP) {
+            tCN[c] += __shfl_xor_sync(0xffffffffu, tCN[c], off);
+            tCD[c] += __shfl_xor_sync(0xffffffffu, tCD[c], off);
+          }
+        }
+      if (lane < Q) {
+        float* tp = a.task_part + (size_t)t * NV;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+          tp[c0 + c] = tN[c];
+          tp[K + c0 + c] = tD[c];
+          if constexpr (HVP) {
+            tp[2 * K + c0 + c] = tCN[c];
+            tp[3 * K + c0 + c] = tCD[c];
+          }
+        }
+      }
+    }
     if (hub) {
-      // publish this chunk's partial row sums; the last chunk adds them up
+      // publish this chunk's partial row sums; the last chunk adds them up.
+      // (sigma_N's share of the row was taken chunk by chunk above, by the
+      // chunk's own warp -- a static assignment, not by whichever finishes last.)
       const int slot_id = task.y;
       if (lead) {
         float* hp = a.hub_part + (size_t)slot_id * 2 * K;
@@ -349,8 +398,6 @@ __global__ void __launch_bounds__(kBlock) edge_kernel(EdgeArgs a) {
           if constexpr (HVP) {
             store_row<K, CPL, VW>(a.out_a, row, c0, rs);
             store_row<K, CPL, VW>(a.out_b, row, c0, rd);
-#pragma unroll
-            for (int c = 0; c < CPL; ++c) accCN[c].add(rd[c] * vi[c]);
           } else {
             store_row<K, CPL, VW>(a.out_a, row, c0, rd);
           }
@@ -372,6 +419,8 @@ __global__ void __launch_bounds__(kBlock) edge_kernel(EdgeArgs a) {
     }
     __syncwarp();
   }
+
+  if (a.task_part) return;  // batches: per-graph sums are reduced by batch_reduce
 
   // warp: lanes of equal q in float-float; lanes 0..Q-1 hold the warp sums
   {

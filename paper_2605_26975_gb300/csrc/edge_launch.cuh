@@ -47,6 +47,7 @@ pspec_status launch_edges_k(pspec_graph* g, const EdgeLaunch& L, cudaStream_t s)
   a.scalars = g->d_scalars;
   a.status = g->d_status;
   a.skip = L.skip;
+  a.task_part = L.task_part;
   int blocks = grid_blocks(g, occ);
   blocks = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (ts.n_tasks + kWarps - 1) / kWarps));
   TimedScope timer(g, HVP ? "hvp_edges" : "eval_edges", s);

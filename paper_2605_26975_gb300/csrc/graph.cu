@@ -127,9 +127,20 @@ pspec_status ensure_tasks(pspec_graph* g, int Q) {
     return e;
   };
   // plain task: x = first sorted row, y = nrows | degree << 8 (all rows of a
-  // task have exactly this degree), z = elog, w = first entry of the task
+  // task have exactly this degree), z = elog, w = first entry of the task.
+  // Rows are sorted within each graph of a batch, and no task crosses a graph.
+  std::vector<int64_t> bounds = g->h_node_off;
+  if (bounds.empty()) bounds = {0, n};
+  std::vector<int32_t> task_graph;
+  std::vector<int32_t> graph_task(bounds.size(), 0);  // first task of each graph
+  size_t gi = 0;
   int64_t r = 0;
   while (r < n) {
+    while (bounds[gi + 1] <= r) {
+      ++gi;
+      graph_task[gi] = (int32_t)tasks.size();
+    }
+    const int64_t gend = bounds[gi + 1];
     const int64_t deg = rp[r + 1] - rp[r];
     if (deg > hub_deg) {
       int nch = (int)((deg + chunk - 1) / chunk);
@@ -143,6 +154,7 @@ pspec_status ensure_tasks(pspec_graph* g, int Q) {
         tasks.push_back(make_int4((int)r, n_chunks + c,
                                   max_elog | (1 << 8) | ((c == 0 ? 1 : 0) << 9) | (int)(len << 10),
                                   (int)(rp[r] + (int64_t)c * chunk)));
+        task_graph.push_back((int32_t)gi);
         chunk_hub.push_back((int32_t)hub_row.size() - 1);
       }
       n_chunks += nch;
@@ -152,10 +164,12 @@ pspec_status ensure_tasks(pspec_graph* g, int Q) {
     const int elog = elog_of(deg);
     const int R = 32 / ((1 << elog) * Q);
     int nrows = 0;
-    while (nrows < R && r + nrows < n && rp[r + nrows + 1] - rp[r + nrows] == deg) ++nrows;
+    while (nrows < R && r + nrows < gend && rp[r + nrows + 1] - rp[r + nrows] == deg) ++nrows;
     tasks.push_back(make_int4((int)r, nrows | (int)(deg << 8), elog, (int)rp[r]));
+    task_graph.push_back((int32_t)gi);
     r += nrows;
   }
+  for (size_t q = gi + 1; q < graph_task.size(); ++q) graph_task[q] = (int32_t)tasks.size();
   ts.Q = Q;
   ts.chunk_edges = chunk;
   ts.n_tasks = (int64_t)tasks.size();
@@ -163,6 +177,14 @@ pspec_status ensure_tasks(pspec_graph* g, int Q) {
   ts.n_chunks = n_chunks;
   PSPEC_CUDA(cudaMalloc(&ts.d_tasks, sizeof(int4) * std::max<size_t>(1, tasks.size())));
   PSPEC_CUDA(cudaMemcpy(ts.d_tasks, tasks.data(), sizeof(int4) * tasks.size(), cudaMemcpyHostToDevice));
+  if (g->n_graphs > 1) {
+    PSPEC_CUDA(cudaMalloc(&ts.d_task_graph, sizeof(int32_t) * std::max<size_t>(1, task_graph.size())));
+    PSPEC_CUDA(cudaMemcpy(ts.d_task_graph, task_graph.data(), sizeof(int32_t) * task_graph.size(),
+                          cudaMemcpyHostToDevice));
+    PSPEC_CUDA(cudaMalloc(&ts.d_graph_task, sizeof(int32_t) * graph_task.size()));
+    PSPEC_CUDA(cudaMemcpy(ts.d_graph_task, graph_task.data(), sizeof(int32_t) * graph_task.size(),
+                          cudaMemcpyHostToDevice));
+  }
   if (ts.n_hubs > 0) {
     PSPEC_CUDA(cudaMalloc(&ts.d_hub_row, sizeof(int32_t) * ts.n_hubs));
     PSPEC_CUDA(cudaMalloc(&ts.d_hub_first, sizeof(int32_t) * ts.n_hubs));
@@ -184,6 +206,12 @@ pspec_status ensure_tasks(pspec_graph* g, int Q) {
   }
   ts.built = true;
   return PSPEC_OK;
+}
+
+int64_t task_count(pspec_graph* g, int k) {
+  const int Q = q_of(k);
+  if (ensure_tasks(g, Q) != PSPEC_OK) return -1;
+  return g->tasks[Q == 1 ? 0 : Q == 2 ? 1 : 2].n_tasks;
 }
 
 pspec_status check_block(const void* ptr, int k, pspec_dtype dtype, const char* name) {
@@ -339,17 +367,32 @@ static pspec_status create_impl(int64_t n, const int64_t* rowptr_in, const int32
     if ((st = copy(g->d_val32, v32.data(), sizeof(float) * nnz)) != PSPEC_OK) return fail(st);
     if ((st = copy(g->d_val64, v64.data(), sizeof(double) * nnz)) != PSPEC_OK) return fail(st);
   }
-  if (!node_off.empty())
+  if (!node_off.empty()) {
     if ((st = copy(g->d_node_off, node_off.data(), sizeof(int64_t) * node_off.size())) != PSPEC_OK)
       return fail(st);
+    std::vector<int32_t> rg(n);
+    for (size_t q = 0; q + 1 < node_off.size(); ++q)
+      for (int64_t i = node_off[q]; i < node_off[q + 1]; ++i) rg[i] = (int32_t)q;
+    cudaError_t e1 = cudaMalloc(&g->d_row_graph, sizeof(int32_t) * n);
+    if (e1 != cudaSuccess) return fail(cuda_error(e1, "cudaMalloc(row_graph)"));
+    e1 = cudaMalloc(&g->d_graph_scalars, sizeof(double) * 128 * (node_off.size() - 1));
+    if (e1 != cudaSuccess) return fail(cuda_error(e1, "cudaMalloc(graph_scalars)"));
+    if ((st = copy(g->d_row_graph, rg.data(), sizeof(int32_t) * n)) != PSPEC_OK) return fail(st);
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    if (e2 != cudaSuccess) return fail(cuda_error(e2, "row_graph upload"));
+  }
   // rows stably sorted by degree: the fast kernels' layout
   {
     std::vector<int32_t> perm(n);
     for (int64_t i = 0; i < n; ++i) perm[i] = (int32_t)i;
     const std::vector<int64_t>& rp0 = g->h_rowptr;
-    std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) {
-      return rp0[a + 1] - rp0[a] < rp0[b + 1] - rp0[b];
-    });
+    // rows of each graph of a batch stay within the graph's range
+    std::vector<int64_t> gb = node_off;
+    if (gb.empty()) gb = {0, n};
+    for (size_t q = 0; q + 1 < gb.size(); ++q)
+      std::stable_sort(perm.begin() + gb[q], perm.begin() + gb[q + 1], [&](int32_t a, int32_t b) {
+        return rp0[a + 1] - rp0[a] < rp0[b + 1] - rp0[b];
+      });
     std::vector<int64_t> rps(n + 1, 0);
     for (int64_t r = 0; r < n; ++r) rps[r + 1] = rps[r] + (rp0[perm[r] + 1] - rp0[perm[r]]);
     std::vector<int32_t> cs(nnz);
@@ -422,6 +465,8 @@ void pspec_graph_destroy(pspec_graph* g) {
     cudaFree(ts.d_hub_nchunk);
     cudaFree(ts.d_hub_ticket);
     cudaFree(ts.d_chunk_hub);
+    cudaFree(ts.d_task_graph);
+    cudaFree(ts.d_graph_task);
   }
   cudaFree(g->d_rowptr);
   cudaFree(g->d_col);
@@ -432,6 +477,9 @@ void pspec_graph_destroy(pspec_graph* g) {
   cudaFree(g->d_val32);
   cudaFree(g->d_val64);
   cudaFree(g->d_node_off);
+  cudaFree(g->d_row_graph);
+  cudaFree(g->d_graph_scalars);
+  cudaFree(g->d_task_part);
   cudaFree(g->d_scratch);
   cudaFree(g->d_hub_part);
   cudaFree(g->d_block_part);

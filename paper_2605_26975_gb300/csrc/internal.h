@@ -34,6 +34,8 @@ struct TaskSet {
   int32_t* d_hub_nchunk = nullptr;  // [n_hubs]
   unsigned* d_hub_ticket = nullptr; // [n_hubs] chunk completion counters
   int32_t* d_chunk_hub = nullptr;   // [n_chunks] hub index of each chunk
+  int32_t* d_task_graph = nullptr;  // [n_tasks] graph of each task (batches)
+  int32_t* d_graph_task = nullptr;  // [G+1] first task of each graph (batches)
 };
 
 struct Timing {
@@ -71,6 +73,10 @@ struct pspec_graph {
   // batched graphs
   std::vector<int64_t> h_node_off;
   int64_t* d_node_off = nullptr;
+  int32_t* d_row_graph = nullptr;     // [n] graph of each vertex
+  double* d_graph_scalars = nullptr;  // [G][128]: N, D, sigma_N, sigma_D, coefficients, F
+  float* d_task_part = nullptr;       // [n_tasks][64] per-task column sums
+  size_t task_part_elems = 0;
   // edge-kernel partitions, one per column split Q in {1, 2, 4}
   pspec::TaskSet tasks[3];
   // workspace
@@ -145,6 +151,7 @@ struct EdgeLaunch {
   float p;
   int k;
   const int* skip = nullptr;  // device flag: when nonzero the launch does nothing
+  float* task_part = nullptr; // batches: per-task column sums (see edge_kernels.cuh)
 };
 pspec_status launch_eval_edges(pspec_graph* g, const EdgeLaunch& a, cudaStream_t s);
 pspec_status launch_hvp_edges(pspec_graph* g, const EdgeLaunch& a, cudaStream_t s);
@@ -160,6 +167,15 @@ pspec_status eval_fast(pspec_graph* g, const float* U, int k, double p, double* 
                        float* grad, double* parts, cudaStream_t s);
 pspec_status hvp_fast(pspec_graph* g, const float* U, const float* V, int k, double p, float* HV,
                       cudaStream_t s, const int* skip = nullptr);
+
+// batches: per-graph scalars, 128 doubles per graph in d_graph_scalars
+constexpr int kGsN = 0, kGsD = 16, kGsC0 = 32, kGsC1 = 48, kGsC2 = 64, kGsC3 = 80, kGsC4 = 96,
+              kGsF = 112, kGsStride = 128;
+pspec_status eval_batched(pspec_graph* g, const float* U, int k, double p, double* F_out,
+                          float* grad, double* parts, cudaStream_t s);
+pspec_status hvp_batched(pspec_graph* g, const float* U, const float* V, int k, double p,
+                         float* HV, cudaStream_t s);
+int64_t task_count(pspec_graph* g, int k);
 
 // scalar slots in d_scalars
 constexpr int kSlotN = 0;      // [16]

@@ -176,6 +176,204 @@ pspec_status hvp_fast(pspec_graph* g, const float* U, const float* V, int k, dou
   return PSPEC_OK;
 }
 
+// ------------------------------------------------------------- batches ---
+// One block per graph: the graph's task slots (contiguous) summed in a fixed
+// order -- each thread a compensated FP32 sum over every (blockDim/NV)-th
+// task, then a float-float tree -- and the graph's FP64 scalars and epilogue
+// coefficients written to gs[graph].
+__global__ void __launch_bounds__(256) batch_reduce(const float* __restrict__ part,
+                                                    const int32_t* __restrict__ graph_task, int K,
+                                                    int NQ, double p, double* gs, int* status) {
+  __shared__ float2 s_part[256];
+  __shared__ double s_tot[64];
+  const int G = blockIdx.x;
+  const int NV = NQ * K;
+  const int parts = blockDim.x / NV;
+  const int v = threadIdx.x % NV, j = threadIdx.x / NV;
+  const int t0 = graph_task[G], t1 = graph_task[G + 1];
+  Kahan acc;
+  acc.init();
+  if (j < parts)
+    for (int t = t0 + j; t < t1; t += parts) acc.add(part[(size_t)t * NV + v]);
+  s_part[threadIdx.x] = kahan_to_ff(acc);
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    float2 tot = make_float2(0.f, 0.f);
+    for (int q = 0; q < parts; ++q) tot = ff_add(tot, s_part[q * NV + threadIdx.x]);
+    s_tot[threadIdx.x] = ff_to_double(tot);
+  }
+  __syncthreads();
+  double* g = gs + (size_t)G * kGsStride;
+  if (threadIdx.x < K) {
+    const int c = threadIdx.x;
+    const double N = 0.5 * s_tot[c], D = s_tot[K + c];
+    const double lam = N / D;
+    g[kGsN + c] = N;
+    g[kGsD + c] = D;
+    int flags = 0;
+    if (!isfinite(N) || !isfinite(D)) flags |= kStatusNonFinite;
+    else if (!(D > 0.0)) flags |= kStatusZeroColumn;
+    if (NQ == 4) {
+      const double sN = s_tot[2 * K + c], sD = s_tot[3 * K + c];
+      g[kGsC0 + c] = p * (p - 1.0) / D;
+      g[kGsC1 + c] = lam;
+      g[kGsC2 + c] = p * p / (D * D);
+      g[kGsC3 + c] = sD;
+      g[kGsC4 + c] = sN - 2.0 * lam * sD;
+    } else {
+      g[kGsC0 + c] = p / D;
+      g[kGsC1 + c] = p * lam / D;
+    }
+    if (flags) atomicOr(status, flags);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double F = 0.0;
+    for (int c = 0; c < K; ++c) F += g[kGsN + c] / g[kGsD + c];
+    g[kGsF] = F;
+  }
+}
+
+// gradient epilogue of a batch: the row's graph picks the coefficients
+template <int VW>
+__global__ void __launch_bounds__(256) grad_epilogue_b(const float* __restrict__ U, float* G,
+                                                       int64_t n_elems, int K,
+                                                       const int32_t* __restrict__ row_graph,
+                                                       const double* __restrict__ gs, float pm2) {
+  const int64_t nv = n_elems / VW;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e0 = v * VW;
+    const int64_t row = e0 / K;
+    const int c = (int)(e0 - row * K);
+    const double* g = gs + (size_t)__ldg(&row_graph[row]) * kGsStride;
+    float u[VW], d[VW];
+    load_vec<VW>(U + e0, u);
+#pragma unroll
+    for (int jj = 0; jj < VW; ++jj) d[jj] = G[e0 + jj];
+#pragma unroll
+    for (int jj = 0; jj < VW; ++jj) {
+      const float phu = abs_pow_pm2_clamped(u[jj], pm2) * u[jj];
+      d[jj] = (float)g[kGsC0 + c + jj] * d[jj] - (float)g[kGsC1 + c + jj] * phu;
+    }
+    store_vec<VW>(G + e0, d);
+  }
+}
+
+template <int VW>
+__global__ void __launch_bounds__(256) hvp_epilogue_b(const float* __restrict__ U,
+                                                      const float* __restrict__ V,
+                                                      const float* __restrict__ Dl, float* HV,
+                                                      int64_t n_elems, int K,
+                                                      const int32_t* __restrict__ row_graph,
+                                                      const double* __restrict__ gs, float pm2) {
+  const bool zero_rule = pm2 != 0.0f;
+  const int64_t nv = n_elems / VW;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e0 = v * VW;
+    const int64_t row = e0 / K;
+    const int c = (int)(e0 - row * K);
+    const double* g = gs + (size_t)__ldg(&row_graph[row]) * kGsStride;
+    float u[VW], x[VW], dl[VW], sv[VW];
+    load_vec<VW>(U + e0, u);
+    load_vec<VW>(V + e0, x);
+    load_vec<VW>(Dl + e0, dl);
+#pragma unroll
+    for (int jj = 0; jj < VW; ++jj) sv[jj] = HV[e0 + jj];
+#pragma unroll
+    for (int jj = 0; jj < VW; ++jj) {
+      const int cc = c + jj;
+      float su = abs_pow_pm2_clamped(u[jj], pm2);
+      const float phu = su * u[jj];
+      if (zero_rule && u[jj] == 0.0f) su = 0.0f;
+      sv[jj] = (float)g[kGsC0 + cc] * (sv[jj] - (float)g[kGsC1 + cc] * su * x[jj]) -
+               (float)g[kGsC2 + cc] * (dl[jj] * (float)g[kGsC3 + cc] + phu * (float)g[kGsC4 + cc]);
+    }
+    store_vec<VW>(HV + e0, sv);
+  }
+}
+
+static pspec_status ensure_task_part(pspec_graph* g, int k) {
+  const int64_t nt = task_count(g, k);
+  if (nt < 0) return set_error(PSPEC_ERR_CUDA, "task partition");
+  const size_t need = (size_t)std::max<int64_t>(1, nt) * 64;
+  if (g->task_part_elems >= need) return PSPEC_OK;
+  if (g->d_task_part) cudaFree(g->d_task_part);
+  g->d_task_part = nullptr;
+  g->task_part_elems = 0;
+  PSPEC_CUDA(cudaMalloc(&g->d_task_part, sizeof(float) * need));
+  g->task_part_elems = need;
+  return PSPEC_OK;
+}
+
+static const int32_t* graph_task_of(pspec_graph* g, int k) {
+  const int Q = q_of(k);
+  return g->tasks[Q == 1 ? 0 : Q == 2 ? 1 : 2].d_graph_task;
+}
+
+pspec_status eval_batched(pspec_graph* g, const float* U, int k, double p, double* F_out, float* grad,
+                          double* parts, cudaStream_t s) {
+  PSPEC_TRY(ensure_task_part(g, k));
+  EdgeLaunch L{U, nullptr, grad, nullptr, (float)p, k, nullptr, g->d_task_part};
+  PSPEC_TRY(launch_eval_edges(g, L, s));
+  const int G = g->n_graphs;
+  {
+    TimedScope timer(g, "batch_reduce", s);
+    batch_reduce<<<G, 256, 0, s>>>(g->d_task_part, graph_task_of(g, k), k, 2, p, g->d_graph_scalars,
+                                   g->d_status);
+    PSPEC_CUDA(cudaGetLastError());
+  }
+  const int64_t ne = g->n * k;
+  const float pm2 = (float)p - 2.0f;
+  {
+    TimedScope timer(g, "grad_epilogue", s);
+    if (k % 4 == 0)
+      grad_epilogue_b<4><<<epi_blocks(g, ne / 4), 256, 0, s>>>(U, grad, ne, k, g->d_row_graph, g->d_graph_scalars, pm2);
+    else if (k % 2 == 0)
+      grad_epilogue_b<2><<<epi_blocks(g, ne / 2), 256, 0, s>>>(U, grad, ne, k, g->d_row_graph, g->d_graph_scalars, pm2);
+    else
+      grad_epilogue_b<1><<<epi_blocks(g, ne), 256, 0, s>>>(U, grad, ne, k, g->d_row_graph, g->d_graph_scalars, pm2);
+    PSPEC_CUDA(cudaGetLastError());
+  }
+  const size_t pitch = sizeof(double) * kGsStride;
+  if (F_out)
+    PSPEC_CUDA(cudaMemcpy2DAsync(F_out, sizeof(double), g->d_graph_scalars + kGsF, pitch, sizeof(double), G,
+                                 cudaMemcpyDeviceToDevice, s));
+  if (parts) {
+    PSPEC_CUDA(cudaMemcpy2DAsync(parts, sizeof(double) * 2 * k, g->d_graph_scalars + kGsN, pitch,
+                                 sizeof(double) * k, G, cudaMemcpyDeviceToDevice, s));
+    PSPEC_CUDA(cudaMemcpy2DAsync(parts + k, sizeof(double) * 2 * k, g->d_graph_scalars + kGsD, pitch,
+                                 sizeof(double) * k, G, cudaMemcpyDeviceToDevice, s));
+  }
+  return PSPEC_OK;
+}
+
+pspec_status hvp_batched(pspec_graph* g, const float* U, const float* V, int k, double p, float* HV,
+                         cudaStream_t s) {
+  const int64_t ne = g->n * k;
+  PSPEC_TRY(ensure_scratch(g, (size_t)ne));
+  PSPEC_TRY(ensure_task_part(g, k));
+  EdgeLaunch L{U, V, HV, g->d_scratch, (float)p, k, nullptr, g->d_task_part};
+  PSPEC_TRY(launch_hvp_edges(g, L, s));
+  {
+    TimedScope timer(g, "batch_reduce", s);
+    batch_reduce<<<g->n_graphs, 256, 0, s>>>(g->d_task_part, graph_task_of(g, k), k, 4, p,
+                                             g->d_graph_scalars, g->d_status);
+    PSPEC_CUDA(cudaGetLastError());
+  }
+  const float pm2 = (float)p - 2.0f;
+  TimedScope timer(g, "hvp_epilogue", s);
+  if (k % 4 == 0)
+    hvp_epilogue_b<4><<<epi_blocks(g, ne / 4), 256, 0, s>>>(U, V, g->d_scratch, HV, ne, k, g->d_row_graph, g->d_graph_scalars, pm2);
+  else if (k % 2 == 0)
+    hvp_epilogue_b<2><<<epi_blocks(g, ne / 2), 256, 0, s>>>(U, V, g->d_scratch, HV, ne, k, g->d_row_graph, g->d_graph_scalars, pm2);
+  else
+    hvp_epilogue_b<1><<<epi_blocks(g, ne), 256, 0, s>>>(U, V, g->d_scratch, HV, ne, k, g->d_row_graph, g->d_graph_scalars, pm2);
+  PSPEC_CUDA(cudaGetLastError());
+  return PSPEC_OK;
+}
+
 }  // namespace pspec
 
 using namespace pspec;
@@ -188,37 +386,41 @@ extern "C" pspec_status pspec_eval(pspec_graph* g, const void* U, int k, double 
                                    void* stream) {
   PSPEC_TRY(check_common(g, k, p));
   if (dtype != PSPEC_F32 && dtype != PSPEC_F64) return set_error(PSPEC_ERR_INVALID_ARG, "bad dtype");
-  if (g->n_graphs != 1) return set_error(PSPEC_ERR_INVALID_ARG, "batched graphs use pspec_eval_batched");
+  if (g->n_graphs != 1 && dtype != PSPEC_F32)
+    return set_error(PSPEC_ERR_INVALID_ARG, "batched graphs run the FP32 path");
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = (size_t)g->n * k * elem_size(dtype);
   const void* dU = U;
   void* dG = grad_out;
   double* dF = F_out;
   double* dP = parts_out;
+  const int G = g->n_graphs;
   if (flags & PSPEC_HOST_PTRS) {
     if (!U || !grad_out) return set_error(PSPEC_ERR_INVALID_ARG, "U or grad_out is NULL");
     const size_t ab = align_up(bytes);
-    PSPEC_TRY(ensure_io(g, 2 * ab + 256 + 8 * 2 * kMaxK));
+    PSPEC_TRY(ensure_io(g, 2 * ab + 256 + 8 * (size_t)G * (1 + 2 * kMaxK)));
     char* base = (char*)g->d_io;
     dU = base;
     dG = base + ab;
     dF = (double*)(base + 2 * ab);
-    dP = dF + 1;
+    dP = dF + G;
     PSPEC_CUDA(cudaMemcpyAsync((void*)dU, U, bytes, cudaMemcpyHostToDevice, s));
   } else {
     PSPEC_TRY(check_block(U, k, dtype, "U"));
     PSPEC_TRY(check_block(grad_out, k, dtype, "grad_out"));
     if (U == grad_out) return set_error(PSPEC_ERR_INVALID_ARG, "grad_out aliases U");
   }
-  if (dtype == PSPEC_F32)
+  if (G > 1)
+    PSPEC_TRY(eval_batched(g, (const float*)dU, k, p, dF, (float*)dG, dP, s));
+  else if (dtype == PSPEC_F32)
     PSPEC_TRY(eval_fast(g, (const float*)dU, k, p, dF, (float*)dG, dP, s));
   else
     PSPEC_TRY(eval_plain64(g, (const double*)dU, k, p, dF, (double*)dG, dP, s));
   if (flags & PSPEC_HOST_PTRS) {
     PSPEC_CUDA(cudaMemcpyAsync(grad_out, dG, bytes, cudaMemcpyDeviceToHost, s));
-    if (F_out) PSPEC_CUDA(cudaMemcpyAsync(F_out, dF, sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (F_out) PSPEC_CUDA(cudaMemcpyAsync(F_out, dF, sizeof(double) * G, cudaMemcpyDeviceToHost, s));
     if (parts_out)
-      PSPEC_CUDA(cudaMemcpyAsync(parts_out, dP, sizeof(double) * 2 * k, cudaMemcpyDeviceToHost, s));
+      PSPEC_CUDA(cudaMemcpyAsync(parts_out, dP, sizeof(double) * 2 * k * G, cudaMemcpyDeviceToHost, s));
     return take_status(g, s);
   }
   return PSPEC_OK;
@@ -228,7 +430,8 @@ extern "C" pspec_status pspec_hvp(pspec_graph* g, const void* U, const void* V, 
                                   pspec_dtype dtype, void* HV_out, unsigned flags, void* stream) {
   PSPEC_TRY(check_common(g, k, p));
   if (dtype != PSPEC_F32 && dtype != PSPEC_F64) return set_error(PSPEC_ERR_INVALID_ARG, "bad dtype");
-  if (g->n_graphs != 1) return set_error(PSPEC_ERR_INVALID_ARG, "batched graphs use pspec_hvp_batched");
+  if (g->n_graphs != 1 && dtype != PSPEC_F32)
+    return set_error(PSPEC_ERR_INVALID_ARG, "batched graphs run the FP32 path");
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = (size_t)g->n * k * elem_size(dtype);
   const void* dU = U;
@@ -250,7 +453,9 @@ extern "C" pspec_status pspec_hvp(pspec_graph* g, const void* U, const void* V, 
     PSPEC_TRY(check_block(HV_out, k, dtype, "HV_out"));
     if (HV_out == U || HV_out == V) return set_error(PSPEC_ERR_INVALID_ARG, "HV_out aliases an input");
   }
-  if (dtype == PSPEC_F32)
+  if (g->n_graphs > 1)
+    PSPEC_TRY(hvp_batched(g, (const float*)dU, (const float*)dV, k, p, (float*)dH, s));
+  else if (dtype == PSPEC_F32)
     PSPEC_TRY(hvp_fast(g, (const float*)dU, (const float*)dV, k, p, (float*)dH, s));
   else
     PSPEC_TRY(hvp_plain64(g, (const double*)dU, (const double*)dV, k, p, (double*)dH, s));

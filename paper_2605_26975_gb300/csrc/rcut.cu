@@ -124,5 +124,6 @@ extern "C" pspec_status pspec_rcut(pspec_graph* g, const int32_t* labels, int n_
                                    double* rcut_out, void* stream) {
   if (!g || !labels || !rcut_out) return set_error(PSPEC_ERR_INVALID_ARG, "NULL argument");
   if (n_clusters < 1 || n_clusters > kRcMaxC) return set_error(PSPEC_ERR_INVALID_ARG, "n_clusters must be in [1, 1024]");
+  if (g->n_graphs != 1) return set_error(PSPEC_ERR_INVALID_ARG, "pspec_rcut takes a single graph");
   return rcut_impl(g, labels, n_clusters, rcut_out, (cudaStream_t)stream);
 }

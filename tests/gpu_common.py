@@ -51,3 +51,48 @@ def small_graphs():
         "hubs": star_plus_powerlaw(),
         "isolated": with_isolated(),
     }
+
+
+def rel_terms(a, ref, scale):
+    """max over columns of ||a_l - ref_l|| / ||scale_l||, with `scale` the
+    elementwise sum of the magnitudes of the terms that make up ref.  This is
+    the rounding bound of a sum of terms: it stays meaningful where the terms
+    cancel (a column of a tiny graph near a stationary point)."""
+    a = np.asarray(a, dtype=np.float64).reshape(ref.shape)
+    num = np.linalg.norm(a - ref, axis=0)
+    den = np.linalg.norm(scale, axis=0)
+    den = np.where(den == 0, 1.0, den)
+    return float(np.max(num / den))
+
+
+def grad_term_scale(oracle, g, U, p):
+    """|(p/D)(Delta_p u)| + |(p/D) lambda phi_p(u)| term by term."""
+    rows, col, w = oracle.edge_list(g)
+    N, D = oracle.objective_parts(g, U, p)
+    out = np.zeros_like(U)
+    for l in range(U.shape[1]):
+        d = np.abs(U[rows, l] - U[col, l])
+        dabs = np.bincount(rows, weights=w * d ** (p - 1.0), minlength=g.n)
+        out[:, l] = (p / D[l]) * (dabs + (N[l] / D[l]) * np.abs(U[:, l]) ** (p - 1.0))
+    return out
+
+
+def hvp_term_scale(oracle, g, U, V, p):
+    """Magnitudes of the terms of the exact Hessian product: the sparse part,
+    the diagonal part and the three rank-two terms, added term by term."""
+    rows, col, w = oracle.edge_list(g)
+    N, D = oracle.objective_parts(g, U, p)
+    c = p * (p - 1.0)
+    out = np.zeros_like(U)
+    for l in range(U.shape[1]):
+        u, v = U[:, l], V[:, l]
+        lam = N[l] / D[l]
+        s = np.bincount(rows, weights=c * w * oracle.abs_pow_pm2(u[rows] - u[col], p)
+                        * np.abs(v[rows] - v[col]), minlength=g.n)
+        diag = lam * c * oracle.abs_pow_pm2(u, p) * np.abs(v)
+        gN = p * oracle.p_laplacian(g, U[:, l:l + 1], p)[:, 0]
+        gD = p * oracle.phi_p(u, p)
+        r2 = (np.abs(gN) * abs(gD @ v) + np.abs(gD) * abs(gN @ v)
+              + 2 * lam * np.abs(gD) * abs(gD @ v)) / D[l] ** 2
+        out[:, l] = (s + diag) / D[l] + r2
+    return out
