@@ -142,6 +142,33 @@ pspec_status pspec_eval(pspec_graph* g, const void* U, int k, double p, pspec_dt
 pspec_status pspec_hvp(pspec_graph* g, const void* U, const void* V, int k, double p,
                        pspec_dtype dtype, void* HV_out, unsigned flags, void* stream);
 
+/* ----------------------------------------------------------------- tune ---
+ * pspec_tune: choose the launch shape of the fused edge kernels for this
+ * handle and column count k by timing them.  Candidates: the edges-per-lane
+ * target L in {Q, 2Q, 4Q, 8Q, 16Q} (Q = column lanes per row for this k; a
+ * row of degree d gets the smallest power-of-two number of edge slots E with
+ * d <= L*E, so L fixes how many rows a warp task holds, 32/(E*Q)) and the
+ * resident blocks per SM (the maximum the kernel's registers allow, and one
+ * fewer).  Each candidate runs one untimed eval + HVP and then `reps` timed
+ * ones on U, V (device, n x k row-major FP32); the fastest is kept on the
+ * handle for every later FP32 call with this k's column split (it changes
+ * the summation order of the per-column sums, within the stated tolerance,
+ * and results stay bit-reproducible for a fixed shape).  The paper has no
+ * counterpart; the shape is a property of the hardware.  Allocates two n x k
+ * FP32 outputs for the duration of the call and synchronises `stream`.
+ * report receives every candidate's mean eval + HVP time.  Errors:
+ * INVALID_ARG (k, p, reps outside [1, 1000], NULL, misalignment), CUDA, OOM. */
+#define PSPEC_TUNE_MAX 16
+typedef struct {
+  int32_t n_candidates;
+  int32_t chosen;                         /* index into the arrays below */
+  int32_t edges_per_lane[PSPEC_TUNE_MAX];
+  int32_t blocks_per_sm[PSPEC_TUNE_MAX];
+  double ms[PSPEC_TUNE_MAX];              /* mean device time of eval + HVP */
+} pspec_tune_report;
+pspec_status pspec_tune(pspec_graph* g, const float* U, const float* V, int k, double p, int reps,
+                        pspec_tune_report* report, void* stream);
+
 /* ------------------------------------------------------ hvp, no allocation ---
  * pspec_hvp_noalloc: the same Hessian-vector product as pspec_hvp (FP32,
  * device pointers), for callers that must not allocate device memory: code

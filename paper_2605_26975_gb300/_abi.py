@@ -43,6 +43,15 @@ class SolveStats(C.Structure):
                 ("eval_calls", C.c_int64), ("seconds", C.c_double), ("kmeans_inertia", C.c_double)]
 
 
+TUNE_MAX = 16
+
+
+class TuneReport(C.Structure):
+    _fields_ = [("n_candidates", C.c_int32), ("chosen", C.c_int32),
+                ("edges_per_lane", C.c_int32 * TUNE_MAX), ("blocks_per_sm", C.c_int32 * TUNE_MAX),
+                ("ms", C.c_double * TUNE_MAX)]
+
+
 _vp = C.c_void_p
 _SIGS = {
     "pspec_graph_create": (C.c_int, [C.c_int64, _vp, _vp, _vp, C.c_int, C.c_uint, _vp, C.POINTER(_vp)]),
@@ -62,6 +71,7 @@ _SIGS = {
     "pspec_rcut": (C.c_int, [_vp, _vp, C.c_int, C.POINTER(C.c_double), _vp]),
     "pspec_hvp_noalloc": (C.c_int, [C.c_int64, _vp, _vp, _vp, _vp, _vp, C.c_int, C.c_double, _vp,
                                     _vp]),
+    "pspec_tune": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_double, C.c_int, C.POINTER(TuneReport), _vp]),
     "pspec_set_timing": (C.c_int, [_vp, C.c_int]),
     "pspec_kernel_times": (C.c_int, [_vp, C.c_char_p, C.c_size_t]),
     "pspec_last_error": (C.c_char_p, []),

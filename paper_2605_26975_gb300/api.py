@@ -128,6 +128,20 @@ class Graph:
         check(st, "pspec_hvp(host)")
         return out
 
+    def tune(self, U, V, p, reps=5):
+        """pspec_tune: time the edge kernels' launch shapes on U, V (FP32 CUDA
+        tensors) and keep the fastest on this handle.  Returns the candidates
+        [(edges_per_lane, blocks_per_sm, ms)] and the chosen index."""
+        U = _dev_block(U, "U", self.n)
+        V = _dev_block(V, "V", self.n)
+        if U.dtype != torch.float32 or V.dtype != torch.float32 or V.shape != U.shape:
+            raise TypeError("U and V must be float32 tensors of the same shape")
+        rep = _abi.TuneReport()
+        check(lib().pspec_tune(self._h, _ptr(U), _ptr(V), U.shape[1], float(p), int(reps),
+                               C.byref(rep), _stream()), "pspec_tune")
+        cands = [(rep.edges_per_lane[i], rep.blocks_per_sm[i], rep.ms[i]) for i in range(rep.n_candidates)]
+        return cands, rep.chosen
+
     def status(self):
         """Synchronise and return (and clear) the kernel-recorded status."""
         return lib().pspec_graph_status(self._h, _stream())

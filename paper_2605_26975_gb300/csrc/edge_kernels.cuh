@@ -10,24 +10,24 @@
 //         and sigma_N = sum_i Delta_i v_i, sigma_D = sum_i phi_p(u_i) v_i.
 //
 // Arithmetic.  Every stored entry (i, j) costs one lg2 and one ex2 per column:
-// w_ij |d|^(p-2) = 2^((p-2) log2|d| + log2 w_ij) with log2 w computed once per
-// entry, then phi = that * d and |d|^p = phi * d.  An exact zero difference
-// gives phi = 0 (the log is clamped, see common.cuh) and, for p < 2, no
-// curvature term in S.
+// w_ij |d|^(p-2) = 2^((p-2) log2|d| + log2 w_ij), with log2 w_ij stored in
+// the graph's sorted copy (computed once, in double, at upload), then
+// phi = that * d and |d|^p = phi * d.  An exact zero difference gives phi = 0
+// (the log is clamped, see common.cuh) and, for p < 2, no curvature term.
 //
 // Data movement.  The kernels read a copy of W whose rows are stably sorted
-// by degree (perm maps a sorted row back to its vertex).  A warp task is a run
-// of consecutive sorted rows of one degree, so its entries are contiguous.
-// Each warp owns a ring of kStages shared-memory stages; lane 0 fills a stage
-// with the task's column indices, weights and perm slice by three TMA bulk
-// copies completing on the stage's mbarrier, kStages tasks ahead of use, so
-// the CSR stream never stalls the lanes: they wait only on the 16-byte
-// gathers of neighbour rows of U (and V).  All barrier waits are bounded; a
-// wait that gives up records a timeout in the status word and the warp stops.
+// by degree (perm maps a sorted row back to its vertex), with each entry's
+// column and log2 weight interleaved in one 8-byte word.  A warp task is a run
+// of consecutive sorted rows of one degree, so its entries are contiguous and
+// every lane knows its exact entry count: the lanes stream their entries
+// with plain 8-byte loads (the warp's loads of one step cover a contiguous
+// window, so they coalesce in L1), the next group's entries are loaded while
+// the current group's neighbour rows are in flight, and the loop has no
+// padding or per-entry bounds test.
 //
 // Work split.  A row is handled by a team of E edge slots x Q column lanes; a
 // lane owns CPL = K/Q consecutive columns (16/8/4-byte vectors).  Typical rows
-// get E = 1 (a lane walks its row UNR entries at a time, no shuffles); longer
+// get E = 1 (a lane walks its row, UNR entries per step, no shuffles); longer
 // rows are shared by E slots and reduced by warp shuffles; rows above the hub
 // threshold are split into chunks whose partial sums the warp finishing the
 // row's last chunk adds in chunk order (atomic ticket, no spinning).
@@ -40,31 +40,12 @@
 
 namespace pspec {
 
-// Entries per lane per row before a row gets more edge slots: 8*Q, so the
-// largest task (32/Q lanes x that) is 256 entries for every column split.
+// Entries per lane per row before a row gets more edge slots: 8*Q, so a hub
+// chunk (32/Q slots x that) is 256 entries for every column split.
 __host__ __device__ constexpr int edges_per_lane(int Q) { return 8 * Q; }
-__host__ __device__ constexpr int task_max_entries(int Q) { return 32 * edges_per_lane(Q) / Q; }
-constexpr int kStages = 3;
-constexpr uint32_t kWaitTries = 2000;  // x up to 1 ms each: about 2 s before a timeout
-
-template <int Q>
-struct StageBuf {
-  static constexpr int SEG = task_max_entries(Q) + 8;  // + alignment slack
-  int4 desc;
-  int32_t col[SEG];
-  float val[SEG];
-  int32_t perm[40];
-};
-
-template <int Q>
-__host__ __device__ constexpr size_t edge_smem_bytes() {
-  return sizeof(StageBuf<Q>) * kStages * kWarps + sizeof(uint64_t) * kStages * kWarps;
-}
 
 struct EdgeArgs {
-  const int64_t* rowptr;  // degree-sorted rows
-  const int32_t* col;
-  const float* val;
+  const int2* cw;         // degree-sorted entries: x = column, y = bits of log2 w
   const int32_t* perm;    // sorted row -> vertex
   const float* U;
   const float* V;
@@ -100,69 +81,131 @@ __device__ __forceinline__ void store_row(float* base, int64_t row, int c0, cons
   for (int j = 0; j < CPL; j += VW) store_vec<VW>(base + row * K + c0 + j, src + j);
 }
 
-// per-lane accumulator: compensated for the objective's sums, plain for the
-// Hessian product's (whose rank-two coefficients need ~1e-6 only)
-template <bool COMP> struct LaneAcc;
-template <> struct LaneAcc<true> {
-  Kahan k;
-  __device__ __forceinline__ void init() { k.init(); }
-  __device__ __forceinline__ void add(float x) { k.add(x); }
-  __device__ __forceinline__ float2 ff() const { return kahan_to_ff(k); }
+// Per-lane running sums of the per-column quantities (N, D and, for the
+// Hessian product, sigma_N and sigma_D): compensated for the objective's
+// sums, plain for the Hessian product's (whose rank-two coefficients need
+// ~1e-6 only).  For a lane of at most 8 columns they live in shared memory,
+// one slot per thread laid out [slot][thread] (a warp's accesses hit 32
+// banks), which frees the registers they would take for occupancy; wider
+// lanes keep them in registers.
+template <int CPL, int NQ, bool COMP, bool SMEM> struct AccBank;
+
+template <int CPL, int NQ, bool COMP>
+struct AccBank<CPL, NQ, COMP, true> {
+  static constexpr int kSlots = NQ * CPL * (COMP ? 2 : 1);
+  float* base;  // this thread's first slot; slot i at base[i * kBlock]
+  __device__ __forceinline__ void init(float* smem) {
+    base = smem + threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < kSlots; ++i) base[i * kBlock] = 0.f;
+  }
+  __device__ __forceinline__ void add(int q, int c, float x) {
+    const int i = q * CPL + c;
+    if constexpr (COMP) {
+      Kahan k{base[(2 * i) * kBlock], base[(2 * i + 1) * kBlock]};
+      k.add(x);
+      base[(2 * i) * kBlock] = k.s;
+      base[(2 * i + 1) * kBlock] = k.c;
+    } else {
+      base[i * kBlock] += x;
+    }
+  }
+  __device__ __forceinline__ float2 ff(int q, int c) const {
+    const int i = q * CPL + c;
+    if constexpr (COMP) return kahan_to_ff(Kahan{base[(2 * i) * kBlock], base[(2 * i + 1) * kBlock]});
+    return make_float2(base[i * kBlock], 0.f);
+  }
 };
-template <> struct LaneAcc<false> {
-  float s;
-  __device__ __forceinline__ void init() { s = 0.f; }
-  __device__ __forceinline__ void add(float x) { s += x; }
-  __device__ __forceinline__ float2 ff() const { return make_float2(s, 0.f); }
+
+template <int CPL, int NQ, bool COMP>
+struct AccBank<CPL, NQ, COMP, false> {
+  static constexpr int kSlots = 1;
+  Kahan k[NQ][CPL];
+  __device__ __forceinline__ void init(float*) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) k[q][c].init();
+  }
+  __device__ __forceinline__ void add(int q, int c, float x) {
+    if constexpr (COMP) k[q][c].add(x);
+    else k[q][c].s += x;
+  }
+  __device__ __forceinline__ float2 ff(int q, int c) const {
+    if constexpr (COMP) return kahan_to_ff(k[q][c]);
+    return make_float2(k[q][c].s, 0.f);
+  }
 };
+
+// Resident blocks per SM the kernel is compiled for: with lanes of at most
+// four columns both kernels fit four blocks of 256 threads (64 registers)
+// without spilling, and the gathers' latency is hidden by that many warps.
+template <int K, bool HVP>
+__host__ __device__ constexpr int edge_min_blocks() {
+  return K / q_of(K) <= 4 ? 4 : 1;
+}
 
 // task descriptor fields (see ensure_tasks)
 __device__ __forceinline__ bool task_is_hub(int4 t) { return ((t.z >> 8) & 1) != 0; }
-__device__ __forceinline__ int task_entries(int4 t) {
-  return task_is_hub(t) ? (t.z >> 10) : (t.y & 0xff) * (t.y >> 8);
-}
-__device__ __forceinline__ int task_rows(int4 t) { return task_is_hub(t) ? 1 : (t.y & 0xff); }
 
-// lane 0: start the three bulk copies of task t into stage st.  Windows are
-// widened to 16-byte granules (the arrays are padded past their ends).
-template <int Q>
-__device__ __forceinline__ void issue_stage(const EdgeArgs& a, int4 t, StageBuf<Q>* st, uint64_t* bar) {
-  st->desc = t;
-  const int cnt = task_entries(t);
-  const int nr = task_rows(t);
-  const int oc = t.w & 3;  // entries before the task in its first granule
-  const int op = t.x & 3;
-  const uint32_t bc = (uint32_t)((oc + cnt + 3) & ~3) * 4u;
-  const uint32_t bp = (uint32_t)((op + nr + 3) & ~3) * 4u;
-  mbar_arrive_expect_tx(bar, (cnt > 0 ? 2u * bc : 0u) + bp);
-  if (cnt > 0) {
-    tma_load_1d(st->col, a.col + (t.w - oc), bc, bar);
-    tma_load_1d(st->val, a.val + (t.w - oc), bc, bar);
+// G entries of a lane's row: gather the neighbour rows, then accumulate
+//   dsum += w phi_p(d),  nsum += w |d|^p,  ssum += w |d|^(p-2) (v_i - v_j)
+template <int K, int CPL, int VW, bool HVP, int G>
+__device__ __forceinline__ void edge_group(const EdgeArgs& a, const int2 (&e)[G], int c0,
+                                           const float (&ui)[CPL], const float (&vi)[CPL], float pm2,
+                                           bool zero_rule, float (&dsum)[CPL], float (&nsum)[CPL],
+                                           float (&ssum)[CPL]) {
+  float uj[G][CPL], vj[G][CPL];
+#pragma unroll
+  for (int u = 0; u < G; ++u) {
+    load_row<K, CPL, VW>(a.U, (int64_t)(uint32_t)e[u].x, c0, uj[u]);
+    if constexpr (HVP) load_row<K, CPL, VW>(a.V, (int64_t)(uint32_t)e[u].x, c0, vj[u]);
   }
-  tma_load_1d(st->perm, a.perm + (t.x - op), bp, bar);
+#pragma unroll
+  for (int u = 0; u < G; ++u) {
+    const float lw = __int_as_float(e[u].y);
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+      const float d = ui[c] - uj[u][c];
+      const float sw = ex2_approx(fmaf(pm2, fmaxf(lg2_approx(fabsf(d)), -126.0f), lw));
+      const float ph = sw * d;  // w phi_p(d)
+      dsum[c] += ph;
+      nsum[c] = fmaf(ph, d, nsum[c]);  // w |d|^p
+      if constexpr (HVP) {
+        const float sz = (zero_rule && d == 0.0f) ? 0.0f : sw;
+        ssum[c] = fmaf(sz, vi[c] - vj[u][c], ssum[c]);
+      }
+    }
+  }
+}
+
+template <int G>
+__device__ __forceinline__ void load_entries(const int2* __restrict__ cw, int E, int2 (&e)[G]) {
+#pragma unroll
+  for (int u = 0; u < G; ++u) e[u] = __ldg(cw + u * E);
 }
 
 template <int K, bool HVP>
-__global__ void __launch_bounds__(kBlock) edge_kernel(EdgeArgs a) {
+__global__ void __launch_bounds__(kBlock, edge_min_blocks<K, HVP>()) edge_kernel(EdgeArgs a) {
   constexpr int Q = q_of(K);
   constexpr int CPL = K / Q;
   constexpr int VW = vw_of(K);
   constexpr int NQ = HVP ? 4 : 2;  // N, D (, sigma_N, sigma_D)
   constexpr int NV = NQ * K;
-  constexpr int UNR = HVP ? (CPL > 8 ? 1 : 2) : (CPL > 8 ? 2 : 4);  // entries per lane per trip
+  constexpr int UNR = HVP ? (CPL > 8 ? 1 : 2) : (CPL > 8 ? 2 : 4);  // entries per lane per step
   constexpr bool COMP = !HVP;
 
+  constexpr bool SMEM_ACC = CPL <= 8;
+  using Acc = AccBank<CPL, NQ, COMP, SMEM_ACC>;
+
   if (a.skip && *a.skip) return;  // uniform over the grid
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ float s_acc[SMEM_ACC ? Acc::kSlots * kBlock : 1];
   __shared__ float2 s_warp[kWarps][NV];
   __shared__ float2 s_blk[NV];
   __shared__ float2 s_tot[NV];
 
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  StageBuf<Q>* stages = reinterpret_cast<StageBuf<Q>*>(smem_raw) + wib * kStages;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + sizeof(StageBuf<Q>) * kStages * kWarps) +
-                   wib * kStages;
   const int q = lane % Q;
   const int c0 = q * CPL;
   const int gwarp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
@@ -170,65 +213,34 @@ __global__ void __launch_bounds__(kBlock) edge_kernel(EdgeArgs a) {
   const float pm2 = a.pm2;
   const bool zero_rule = pm2 != 0.0f;  // p < 2: a zero difference has no curvature
 
-  LaneAcc<COMP> accN[CPL], accD[CPL];
-  LaneAcc<false> accCN[HVP ? CPL : 1], accCD[HVP ? CPL : 1];
-#pragma unroll
-  for (int c = 0; c < CPL; ++c) {
-    accN[c].init();
-    accD[c].init();
-    if constexpr (HVP) {
-      accCN[c].init();
-      accCD[c].init();
-    }
-  }
+  Acc acc;
+  acc.init(s_acc);
 
-  // ---- prologue: barriers, then the first kStages tasks of this warp in flight
-  if (lane == 0) {
-    for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
-    mbar_init_fence();
-    for (int s = 0; s < kStages; ++s) {
-      const int t = gwarp + s * nwarps;
-      if (t < a.n_tasks) issue_stage<Q>(a, __ldg(&a.tasks[t]), &stages[s], &bars[s]);
-    }
-  }
-  __syncwarp();
-
-  uint32_t phase = 0;  // bit s: parity of the next completion of stage s
-  bool timed_out = false;
-  int it = 0;
-  for (int t = gwarp; t < a.n_tasks; t += nwarps, ++it) {
-    const int s = it % kStages;
-    // every lane observes the completion itself (acquire); the decision to go
-    // on is taken by the whole warp
-    const bool got = mbar_wait_bounded(&bars[s], (phase >> s) & 1u, kWaitTries);
-    if (!__all_sync(0xffffffffu, got)) {
-      timed_out = true;
-      break;
-    }
-    phase ^= 1u << s;
-    StageBuf<Q>& st = stages[s];
-    const int4 task = st.desc;
+  for (int t = gwarp; t < a.n_tasks; t += nwarps) {
+    const int4 task = __ldg(&a.tasks[t]);
     const bool hub = task_is_hub(task);
     const int elog = task.z & 0xff;
     const int E = 1 << elog;
     const int T = E * Q;
     const int team = lane / T;
     const int slot = (lane % T) / Q;
-    const int oc = task.w & 3;
-    const int op = task.x & 3;
-    int l_beg, l_end;  // entries of this lane's row within the stage
+    int cnt, start;  // entries of this lane's row (or hub chunk) and the first of them
     bool active;
     if (!hub) {
       const int deg = task.y >> 8;
       active = team < (task.y & 0xff);
-      l_beg = oc + team * deg;
-      l_end = l_beg + deg;
+      cnt = deg;
+      start = task.w + team * deg;
     } else {
       active = true;
-      l_beg = oc;
-      l_end = oc + (task.z >> 10);
+      cnt = task.z >> 10;
+      start = task.w;
     }
-    const int64_t row = active ? (int64_t)st.perm[op + (hub ? 0 : team)] : 0;
+    const int n_my = (active && slot < cnt) ? ((cnt - slot + E - 1) >> elog) : 0;
+    const int2* cw = a.cw + start + slot;  // this lane's entries: cw[j * E], j < n_my
+    int2 nx[UNR];
+    if (n_my >= UNR) load_entries<UNR>(cw, E, nx);
+    const int64_t row = active ? (int64_t)__ldg(&a.perm[task.x + (hub ? 0 : team)]) : 0;
 
     float ui[CPL], vi[CPL], dsum[CPL], nsum[CPL], ssum[CPL];
 #pragma unroll
@@ -236,48 +248,28 @@ __global__ void __launch_bounds__(kBlock) edge_kernel(EdgeArgs a) {
     if (active) {
       load_row<K, CPL, VW>(a.U, row, c0, ui);
       if constexpr (HVP) load_row<K, CPL, VW>(a.V, row, c0, vi);
-      for (int e = l_beg + slot; e < l_end; e += UNR * E) {
-        int jj[UNR];
-        float lw[UNR];
+    }
+    int j = 0;
+    for (; j + UNR <= n_my; j += UNR) {
+      int2 e[UNR];
 #pragma unroll
-        for (int u = 0; u < UNR; ++u) {
-          const int eu = e + u * E;
-          const bool ok = eu < l_end;
-          jj[u] = ok ? st.col[eu] : (int)row;  // off the end: own row, weight 0
-          lw[u] = ok ? st.val[eu] : 0.0f;
-        }
-        float uj[UNR][CPL], vj[UNR][CPL];
-#pragma unroll
-        for (int u = 0; u < UNR; ++u) {
-          load_row<K, CPL, VW>(a.U, jj[u], c0, uj[u]);
-          if constexpr (HVP) load_row<K, CPL, VW>(a.V, jj[u], c0, vj[u]);
-        }
-#pragma unroll
-        for (int u = 0; u < UNR; ++u) lw[u] = lg2_approx(lw[u]);  // log2 0 = -inf: no contribution
-#pragma unroll
-        for (int u = 0; u < UNR; ++u) {
-#pragma unroll
-          for (int c = 0; c < CPL; ++c) {
-            const float d = ui[c] - uj[u][c];
-            const float sw = ex2_approx(fmaf(pm2, fmaxf(lg2_approx(fabsf(d)), -126.0f), lw[u]));
-            const float ph = sw * d;  // w phi_p(d)
-            dsum[c] += ph;
-            nsum[c] = fmaf(ph, d, nsum[c]);  // w |d|^p
-            if constexpr (HVP) {
-              const float sz = (zero_rule && d == 0.0f) ? 0.0f : sw;
-              ssum[c] = fmaf(sz, vi[c] - vj[u][c], ssum[c]);
-            }
-          }
-        }
+      for (int u = 0; u < UNR; ++u) e[u] = nx[u];
+      if (j + 2 * UNR <= n_my) load_entries<UNR>(cw + (j + UNR) * E, E, nx);  // next step's entries
+      edge_group<K, CPL, VW, HVP, UNR>(a, e, c0, ui, vi, pm2, zero_rule, dsum, nsum, ssum);
+    }
+    if constexpr (UNR >= 4) {
+      if (n_my - j >= 2) {
+        int2 e[2];
+        load_entries<2>(cw + j * E, E, e);
+        edge_group<K, CPL, VW, HVP, 2>(a, e, c0, ui, vi, pm2, zero_rule, dsum, nsum, ssum);
+        j += 2;
       }
     }
-    // every lane has read the stage: refill it with this warp's task kStages ahead
-    __syncwarp();
-    if (lane == 0) {
-      const int tn = t + kStages * nwarps;
-      if (tn < a.n_tasks) {
-        fence_proxy_async_smem();
-        issue_stage<Q>(a, __ldg(&a.tasks[tn]), &st, &bars[s]);
+    if constexpr (UNR >= 2) {
+      if (j < n_my) {  // at most one entry left
+        int2 e[1];
+        load_entries<1>(cw + j * E, E, e);
+        edge_group<K, CPL, VW, HVP, 1>(a, e, c0, ui, vi, pm2, zero_rule, dsum, nsum, ssum);
       }
     }
     // row sums across the E edge slots of each team (lanes of equal q)
@@ -323,11 +315,11 @@ __global__ void __launch_bounds__(kBlock) edge_kernel(EdgeArgs a) {
       if (lead) {
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
-          accN[c].add(tN[c]);
-          accD[c].add(tD[c]);
+          acc.add(0, c, tN[c]);
+          acc.add(1, c, tD[c]);
           if constexpr (HVP) {
-            accCN[c].add(tCN[c]);
-            accCD[c].add(tCD[c]);
+            acc.add(2, c, tCN[c]);
+            acc.add(3, c, tCD[c]);
           }
         }
       }
@@ -406,20 +398,6 @@ __global__ void __launch_bounds__(kBlock) edge_kernel(EdgeArgs a) {
       }
     }
   }
-  if (timed_out) {
-    // drain this warp's copies still in flight (bounded), then report
-    if (lane == 0) {
-      atomicOr(a.status, kStatusTimeout);
-      int t = gwarp + it * nwarps;
-      for (int k2 = 0; k2 < kStages && t < a.n_tasks; ++k2, ++it, t += nwarps) {
-        const int s = it % kStages;
-        mbar_wait_bounded(&bars[s], (phase >> s) & 1u, kWaitTries);
-        phase ^= 1u << s;
-      }
-    }
-    __syncwarp();
-  }
-
   if (a.task_part) return;  // batches: per-graph sums are reduced by batch_reduce
 
   // warp: lanes of equal q in float-float; lanes 0..Q-1 hold the warp sums
@@ -427,12 +405,8 @@ __global__ void __launch_bounds__(kBlock) edge_kernel(EdgeArgs a) {
     float2 v[NQ][CPL];
 #pragma unroll
     for (int c = 0; c < CPL; ++c) {
-      v[0][c] = accN[c].ff();
-      v[1][c] = accD[c].ff();
-      if constexpr (HVP) {
-        v[2][c] = accCN[c].ff();
-        v[3][c] = accCD[c].ff();
-      }
+#pragma unroll
+      for (int qq = 0; qq < NQ; ++qq) v[qq][c] = acc.ff(qq, c);
     }
 #pragma unroll
     for (int off = Q; off < 32; off <<= 1)

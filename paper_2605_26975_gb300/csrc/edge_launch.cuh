@@ -14,19 +14,15 @@ template <int K, bool HVP>
 pspec_status launch_edges_k(pspec_graph* g, const EdgeLaunch& L, cudaStream_t s) {
   constexpr int Q = q_of(K);
   PSPEC_TRY(ensure_tasks(g, Q));
-  const TaskSet& ts = g->tasks[Q == 1 ? 0 : Q == 2 ? 1 : 2];
-  constexpr size_t smem = edge_smem_bytes<Q>();
+  const TaskSet& ts = g->tasks[q_index(Q)];
   static int occ = -1;
   if (occ < 0) {
-    PSPEC_CUDA(cudaFuncSetAttribute(edge_kernel<K, HVP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    PSPEC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, edge_kernel<K, HVP>, kBlock, smem));
+    PSPEC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, edge_kernel<K, HVP>, kBlock, 0));
     occ = std::max(occ, 1);
     if (const char* env = std::getenv("PSPEC_EDGE_BLOCKS_PER_SM")) occ = std::max(1, std::min(occ, std::atoi(env)));
   }
   EdgeArgs a;
-  a.rowptr = g->d_rowptr_s;
-  a.col = g->d_col_s;
-  a.val = g->d_val32_s;
+  a.cw = g->d_cw_s;
   a.perm = g->d_perm;
   a.U = L.U;
   a.V = L.V;
@@ -48,11 +44,18 @@ pspec_status launch_edges_k(pspec_graph* g, const EdgeLaunch& L, cudaStream_t s)
   a.status = g->d_status;
   a.skip = L.skip;
   a.task_part = L.task_part;
-  int blocks = grid_blocks(g, occ);
+  const int want = g->edge_blocks_per_sm[q_index(Q)];
+  int blocks = grid_blocks(g, want > 0 ? std::min(want, occ) : occ);
   blocks = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (ts.n_tasks + kWarps - 1) / kWarps));
   TimedScope timer(g, HVP ? "hvp_edges" : "eval_edges", s);
-  edge_kernel<K, HVP><<<blocks, kBlock, smem, s>>>(a);
+  edge_kernel<K, HVP><<<blocks, kBlock, 0, s>>>(a);
   PSPEC_CUDA(cudaGetLastError());
+  return PSPEC_OK;
+}
+
+template <int K, bool HVP>
+pspec_status occupancy_k(int* blocks_per_sm) {
+  PSPEC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, edge_kernel<K, HVP>, kBlock, 0));
   return PSPEC_OK;
 }
 
@@ -62,4 +65,6 @@ pspec_status launch_edges_k(pspec_graph* g, const EdgeLaunch& L, cudaStream_t s)
   template pspec_status pspec::launch_edges_k<K, false>(pspec_graph*, const pspec::EdgeLaunch&, \
                                                         cudaStream_t);                      \
   template pspec_status pspec::launch_edges_k<K, true>(pspec_graph*, const pspec::EdgeLaunch&,  \
-                                                       cudaStream_t);
+                                                       cudaStream_t);                      \
+  template pspec_status pspec::occupancy_k<K, false>(int*);                                 \
+  template pspec_status pspec::occupancy_k<K, true>(int*);

@@ -103,13 +103,26 @@ static int env_int(const char* name, int dflt) {
 // of two with d <= L*E (L = target edges per lane); a task takes up to
 // 32/(E*Q) consecutive sorted rows of the same E.  Rows longer than
 // hub_deg are split into chunks of chunk_edges entries.
+void free_tasks(TaskSet& ts) {
+  cudaFree(ts.d_tasks);
+  cudaFree(ts.d_hub_row);
+  cudaFree(ts.d_hub_first);
+  cudaFree(ts.d_hub_nchunk);
+  cudaFree(ts.d_hub_ticket);
+  cudaFree(ts.d_chunk_hub);
+  cudaFree(ts.d_task_graph);
+  cudaFree(ts.d_graph_task);
+  ts = TaskSet();
+}
+
 pspec_status ensure_tasks(pspec_graph* g, int Q) {
   int qi = Q == 1 ? 0 : Q == 2 ? 1 : 2;
   TaskSet& ts = g->tasks[qi];
   if (ts.built) return PSPEC_OK;
-  // at most edges_per_lane(Q) entries per lane: a task never exceeds
-  // task_max_entries(Q), the size of the kernels' shared-memory stages
-  const int L = std::max(1, std::min(edges_per_lane(Q), env_int("PSPEC_EDGES_PER_LANE", edges_per_lane(Q))));
+  // at most edges_per_lane(Q) entries per lane and row before the row gets
+  // more edge slots; hub chunks give each lane that many entries
+  const int L = std::max(1, g->edges_per_lane[qi] > 0 ? g->edges_per_lane[qi]
+                                                      : env_int("PSPEC_EDGES_PER_LANE", edges_per_lane(Q)));
   const int max_slots = 32 / Q;
   int max_elog = 0;
   while ((1 << max_elog) < max_slots) ++max_elog;
@@ -395,28 +408,27 @@ static pspec_status create_impl(int64_t n, const int64_t* rowptr_in, const int32
       });
     std::vector<int64_t> rps(n + 1, 0);
     for (int64_t r = 0; r < n; ++r) rps[r + 1] = rps[r] + (rp0[perm[r] + 1] - rp0[perm[r]]);
-    std::vector<int32_t> cs(nnz);
-    std::vector<float> vs(nnz);
+    // {column, log2 of the FP32 weight rounded to FP32}: the kernels form
+    // w |d|^(p-2) as one power of two (a zero weight gives -inf, hence 0)
+    std::vector<int2> cw(nnz);
     for (int64_t r = 0; r < n; ++r) {
       const int64_t src = rp0[perm[r]], len = rps[r + 1] - rps[r];
-      std::copy(col.begin() + src, col.begin() + src + len, cs.begin() + rps[r]);
-      std::copy(v32.begin() + src, v32.begin() + src + len, vs.begin() + rps[r]);
+      for (int64_t q = 0; q < len; ++q) {
+        const float lw = (float)std::log2((double)v32[src + q]);
+        int bits;
+        std::memcpy(&bits, &lw, sizeof(bits));
+        cw[rps[r] + q] = make_int2(col[src + q], bits);
+      }
     }
     auto alloc = [&](void** p, size_t bytes) {
       cudaError_t e = cudaMalloc(p, bytes);
       return e == cudaSuccess ? PSPEC_OK : cuda_error(e, "cudaMalloc(sorted CSR)");
     };
-    if ((st = alloc((void**)&g->d_rowptr_s, sizeof(int64_t) * (n + 1))) != PSPEC_OK) return fail(st);
-    // padded by 64 bytes: the edge kernels prefetch 16-byte-rounded windows
-    if ((st = alloc((void**)&g->d_col_s, sizeof(int32_t) * (nnz + 16))) != PSPEC_OK) return fail(st);
-    if ((st = alloc((void**)&g->d_val32_s, sizeof(float) * (nnz + 16))) != PSPEC_OK) return fail(st);
+    if ((st = alloc((void**)&g->d_cw_s, sizeof(int2) * (nnz + 16))) != PSPEC_OK) return fail(st);
     if ((st = alloc((void**)&g->d_perm, sizeof(int32_t) * (n + 16))) != PSPEC_OK) return fail(st);
-    if ((st = copy(g->d_rowptr_s, rps.data(), sizeof(int64_t) * (n + 1))) != PSPEC_OK) return fail(st);
     if ((st = copy(g->d_perm, perm.data(), sizeof(int32_t) * n)) != PSPEC_OK) return fail(st);
-    if (nnz) {
-      if ((st = copy(g->d_col_s, cs.data(), sizeof(int32_t) * nnz)) != PSPEC_OK) return fail(st);
-      if ((st = copy(g->d_val32_s, vs.data(), sizeof(float) * nnz)) != PSPEC_OK) return fail(st);
-    }
+    if (nnz)
+      if ((st = copy(g->d_cw_s, cw.data(), sizeof(int2) * nnz)) != PSPEC_OK) return fail(st);
     cudaError_t e2 = cudaStreamSynchronize(s);  // the host vectors go out of scope
     if (e2 != cudaSuccess) return fail(cuda_error(e2, "sorted CSR upload"));
     g->h_rowptr_s = std::move(rps);
@@ -459,20 +471,11 @@ pspec_status pspec_graph_create_batched(int32_t n_graphs, const int64_t* node_of
 void pspec_graph_destroy(pspec_graph* g) {
   if (!g) return;
   for (auto& ts : g->tasks) {
-    cudaFree(ts.d_tasks);
-    cudaFree(ts.d_hub_row);
-    cudaFree(ts.d_hub_first);
-    cudaFree(ts.d_hub_nchunk);
-    cudaFree(ts.d_hub_ticket);
-    cudaFree(ts.d_chunk_hub);
-    cudaFree(ts.d_task_graph);
-    cudaFree(ts.d_graph_task);
+    free_tasks(ts);
   }
   cudaFree(g->d_rowptr);
   cudaFree(g->d_col);
-  cudaFree(g->d_rowptr_s);
-  cudaFree(g->d_col_s);
-  cudaFree(g->d_val32_s);
+  cudaFree(g->d_cw_s);
   cudaFree(g->d_perm);
   cudaFree(g->d_val32);
   cudaFree(g->d_val64);

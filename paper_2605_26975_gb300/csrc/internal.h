@@ -63,10 +63,9 @@ struct pspec_graph {
   double* d_val64 = nullptr;
   std::vector<int64_t> h_rowptr;     // host copy (task building, batching)
   // the same matrix with its rows stably sorted by degree (fast edge kernels):
-  // sorted row r is row d_perm[r] of W; column indices are unchanged
-  int64_t* d_rowptr_s = nullptr;
-  int32_t* d_col_s = nullptr;
-  float* d_val32_s = nullptr;
+  // sorted row r is row d_perm[r] of W; column indices are unchanged; each
+  // entry is one 8-byte word {column, bits of (float)log2(w)}
+  int2* d_cw_s = nullptr;
   int32_t* d_perm = nullptr;
   std::vector<int64_t> h_rowptr_s;
   std::vector<int32_t> h_perm;
@@ -79,6 +78,11 @@ struct pspec_graph {
   size_t task_part_elems = 0;
   // edge-kernel partitions, one per column split Q in {1, 2, 4}
   pspec::TaskSet tasks[3];
+  // launch shape per column split (index q_index(Q)); 0 = built-in default.
+  // Set by pspec_tune or the PSPEC_EDGES_PER_LANE / PSPEC_EDGE_BLOCKS_PER_SM
+  // environment variables.
+  int edges_per_lane[3] = {0, 0, 0};
+  int edge_blocks_per_sm[3] = {0, 0, 0};
   // workspace
   float* d_scratch = nullptr;        // n x 16 floats (HVP's Delta rows)
   size_t scratch_elems = 0;
@@ -136,6 +140,8 @@ struct TimedScope {
 
 // task sets and workspace
 pspec_status ensure_tasks(pspec_graph* g, int Q);
+void free_tasks(TaskSet& ts);
+inline int q_index(int Q) { return Q == 1 ? 0 : Q == 2 ? 1 : 2; }
 pspec_status ensure_io(pspec_graph* g, size_t bytes);
 int grid_blocks(pspec_graph* g, int blocks_per_sm);
 pspec_status check_block(const void* ptr, int k, pspec_dtype dtype, const char* name);
@@ -153,6 +159,7 @@ struct EdgeLaunch {
   const int* skip = nullptr;  // device flag: when nonzero the launch does nothing
   float* task_part = nullptr; // batches: per-task column sums (see edge_kernels.cuh)
 };
+pspec_status edge_occupancy(int k, bool hvp, int* blocks_per_sm);
 pspec_status launch_eval_edges(pspec_graph* g, const EdgeLaunch& a, cudaStream_t s);
 pspec_status launch_hvp_edges(pspec_graph* g, const EdgeLaunch& a, cudaStream_t s);
 

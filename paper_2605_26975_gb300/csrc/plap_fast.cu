@@ -27,6 +27,22 @@ static pspec_status dispatch_edges(pspec_graph* g, const EdgeLaunch& L, cudaStre
   }
 }
 
+template <int K, bool HVP>
+pspec_status occupancy_k(int* blocks_per_sm);
+
+pspec_status edge_occupancy(int k, bool hvp, int* blocks_per_sm) {
+  switch (k) {
+#define CASE(K) \
+  case K:       \
+    return hvp ? occupancy_k<K, true>(blocks_per_sm) : occupancy_k<K, false>(blocks_per_sm);
+    CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+    CASE(9) CASE(10) CASE(11) CASE(12) CASE(13) CASE(14) CASE(15) CASE(16)
+#undef CASE
+    default:
+      return set_error(PSPEC_ERR_INVALID_ARG, "k must be in [1, 16]");
+  }
+}
+
 pspec_status launch_eval_edges(pspec_graph* g, const EdgeLaunch& L, cudaStream_t s) {
   return dispatch_edges<false>(g, L, s);
 }
