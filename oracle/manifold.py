@@ -19,6 +19,9 @@ Grassmann geometry):
   * outer method: trust-region Newton (radius update 1/4 and 3/4 rules,
     acceptance when rho > rho_prime and the model decreased), with the
     ratio rho regularised by rho_reg * max(1, |f|) on both sides;
+  * Euclidean Hessian: the exact Hessian of the quotient N/D by default;
+    optionally (hessian="alg1") only the sparse-plus-diagonal matrix that
+    Algorithm 1 applies, without the quotient's rank-two terms;
   * inner method: Steihaug-Toint truncated CG from eta = 0 without a
     preconditioner, stopping on negative curvature, on reaching the radius,
     when ||r|| <= ||r_0|| min(||r_0||^theta, kappa), or after max_inner steps;
@@ -57,6 +60,9 @@ class SolveOptions:
     kmeans_restarts: int = 10
     kmeans_max_iter: int = 300
     seed: int = 0
+    # "exact": the Hessian of the quotient N/D (sparse + diagonal + rank-two
+    # terms); "alg1": only the sparse-plus-diagonal matrix Algorithm 1 applies
+    hessian: str = "exact"
 
 
 def inner(A, B):
@@ -141,8 +147,10 @@ def rtr_newton(g, U, p, opts: SolveOptions):
             break
         outer += 1
 
+        ehvp = plap.alg1_sparse_hvp if opts.hessian == "alg1" else plap.euclidean_hvp
+
         def hess(eta, U=U, egrad=egrad):
-            return riemannian_hessian(U, egrad, plap.euclidean_hvp(g, U, eta, p), eta)
+            return riemannian_hessian(U, egrad, ehvp(g, U, eta, p), eta)
 
         eta, Heta, its, _reason, on_boundary = tcg(hess, rg, Delta, opts.theta,
                                                    opts.kappa, opts.max_inner)

@@ -151,3 +151,31 @@ def test_sbm4_continuation_recovers_blocks_and_descends():
     # RCut of the p-final clustering is no worse than the p = 2 stage's
     U2, lab2, rc2, _ = oracle.solve(g, U0, (2.0,))
     assert rc <= rc2 * (1 + 1e-9)
+
+
+def test_alg1_hessian_form_is_exact_on_tangent_vectors_at_p2():
+    """Algorithm 1 applies only the sparse-plus-diagonal part of the
+    quotient's Hessian.  At p = 2 the dropped rank-two terms of column l are
+    combinations of u_l (since <g_D, eta> = 2<u_l, eta_l> = 0 for tangent eta
+    and g_D = 2 u_l), so the tangent projection removes them: the Riemannian
+    Hessians of the two forms agree, and so do the p = 2 solves (Ky Fan)."""
+    rng = np.random.default_rng(12)
+    n, k = 40, 3
+    A = np.triu((rng.random((n, n)) < 0.2) * rng.uniform(0.5, 1.5, (n, n)), 1)
+    Wd = A + A.T
+    g = dense_graph(Wd)
+    U = wl.orthonormal_block(4, n, k, np.float64)
+    eta = oracle.project(U, rng.standard_normal((n, k)))
+    egrad = oracle.euclidean_grad(g, U, 2.0)
+    h_exact = oracle.riemannian_hessian(U, egrad, oracle.euclidean_hvp(g, U, eta, 2.0), eta)
+    h_alg1 = oracle.riemannian_hessian(U, egrad, oracle.alg1_sparse_hvp(g, U, eta, 2.0), eta)
+    assert np.allclose(h_alg1, h_exact, rtol=0, atol=1e-12 * np.abs(h_exact).max())
+    # for p < 2 the forms differ (the rank-two terms have tangent parts)
+    egrad = oracle.euclidean_grad(g, U, 1.5)
+    d = oracle.riemannian_hessian(U, egrad, oracle.euclidean_hvp(g, U, eta, 1.5)
+                                  - oracle.alg1_sparse_hvp(g, U, eta, 1.5), 0 * eta)
+    assert np.linalg.norm(d) > 1e-6 * np.linalg.norm(h_exact)
+    opts = oracle.SolveOptions(max_outer=60, gtol_rel=1e-9, hessian="alg1")
+    U1, st = oracle.rtr_newton(g, wl.orthonormal_block(9, n, k, np.float64), 2.0, opts)
+    ev = np.linalg.eigvalsh(laplacian(Wd))
+    assert math.isclose(oracle.objective(g, U1, 2.0), ev[:k].sum(), rel_tol=1e-8)
