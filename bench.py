@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--eager", action="store_true", help="launch the step's kernels one by one")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape (no pspec_tune)")
     return ap.parse_args()
 
 
@@ -361,19 +362,19 @@ def main():
             pt.G.eval(pt.Ud, P_BENCH, grad_out=pt.grad)
             pt.G.hvp(pt.Ud, pt.Vd, P_BENCH, out=pt.HV)
 
+    # launch shape per handle from the autotuner (edges per lane, blocks per SM)
+    tuned = []
+    for pt in parts:
+        if not args.no_tune:
+            cands, best = pt.G.tune(pt.Ud, pt.Vd, P_BENCH, reps=3)
+            L, b, ms = cands[best]
+            tuned.append({"k": pt.k, "edges_per_lane": L, "blocks_per_sm": b,
+                          "eval_hvp_ms": round(ms, 4), "candidates": len(cands)})
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
     for pt in parts:
         assert pt.G.status() == 0
-    if args.steps is None:  # about 2 s of timed region, from one timed warm-up step
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        flush.zero_()
-        step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        args.steps = int(min(20000, max(50, 2000.0 / max(e0.elapsed_time(e1), 1e-3))))
     # the step (per handle eval + hvp: 4 kernel launches, 6 for a batch)
     # replayed as one CUDA graph, so host launch latency does not sit between
     # the kernels
@@ -387,6 +388,22 @@ def main():
         run_step = graph.replay
     else:
         run_step = step
+
+    if args.steps is None:  # about 2 s of timed region, from five timed steps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(5):
+            flush.zero_()
+            run_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        per_step = e0.elapsed_time(e1) / 5
+        args.steps = int(min(20000, max(50, 2000.0 / max(per_step, 1e-3))))
+        if world > 1:  # every rank times the same number of steps: rank 0's
+            kt = torch.tensor([args.steps], dtype=torch.int64, device="cuda")
+            dist.broadcast(kt, 0)
+            args.steps = int(kt.item())
 
     # ---- timed region: device time of every step, L2 flushed before each
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -518,6 +535,7 @@ def main():
                        "step": "pspec_eval (F + grad) + pspec_hvp" + (" per handle" if len(parts) > 1 else "")
                                + ("" if args.eager else ", replayed as a CUDA graph"),
                        "l2": "flushed (256 MB write) before every timed step",
+                       "launch_shape": tuned if tuned else "default (not tuned)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches * args.steps, "solve": solve,

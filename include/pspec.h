@@ -69,6 +69,7 @@ typedef enum { PSPEC_F32 = 0, PSPEC_F64 = 1 } pspec_dtype;
 /* flags */
 #define PSPEC_HOST_PTRS 0x1u      /* pointer arguments are host memory         */
 #define PSPEC_CHECK_SYMMETRY 0x2u /* graph_create: verify w_ij == w_ji (host)  */
+#define PSPEC_HVP_ALG1 0x4u       /* hvp: Algorithm 1's form (see pspec_hvp)   */
 
 typedef struct pspec_graph pspec_graph;
 
@@ -138,7 +139,10 @@ pspec_status pspec_eval(pspec_graph* g, const void* U, int k, double p, pspec_dt
  * The sparse-plus-diagonal part is what Algorithm 1 applies column by
  * column; the rank-two terms complete the Hessian of the quotient.
  * On a batched graph lambda, D, g_N and g_D are each graph's own (FP32
- * only, as pspec_eval).  HV_out may not alias U or V.  Errors as pspec_eval. */
+ * only, as pspec_eval).  With PSPEC_HVP_ALG1 in flags the rank-two terms
+ * are left out: HV = (Hess N V - lambda Hess D V)/D per column, the sparse
+ * (W's pattern) plus diagonal matrix that Algorithm 1 applies.  HV_out may
+ * not alias U or V.  Errors as pspec_eval. */
 pspec_status pspec_hvp(pspec_graph* g, const void* U, const void* V, int k, double p,
                        pspec_dtype dtype, void* HV_out, unsigned flags, void* stream);
 
@@ -204,8 +208,14 @@ pspec_status pspec_hvp_noalloc(int64_t n, const int64_t* rowptr, const int32_t* 
  *             final U out
  *   labels_out device int32[n] (may be NULL), rcut_out host double (may be
  *             NULL), stats host (may be NULL).
- * Synchronises `stream`.  Returns OK, or NOT_CONVERGED when a stage hit
- * max_outer (the result is still written).  Not for batched graphs. */
+ * The solve runs on a private stream of the handle, after the work already
+ * enqueued on `stream`, and returns once it is complete; `stream`'s later
+ * work is ordered after it.  Chunks of truncated-CG iterations are replayed
+ * as CUDA graphs (eagerly launched while kernel timing is on).  Returns OK,
+ * or NOT_CONVERGED when a stage hit max_outer (the result is still
+ * written).  Not for batched graphs; calls on one handle must not overlap. */
+#define PSPEC_HESSIAN_EXACT 0 /* the exact Hessian of the quotient N/D        */
+#define PSPEC_HESSIAN_ALG1 1  /* Algorithm 1's sparse-plus-diagonal form     */
 typedef struct {
   int32_t max_outer;       /* Newton steps per p (default 30)                 */
   int32_t max_inner;       /* truncated-CG steps per Newton step (50)         */
@@ -221,6 +231,8 @@ typedef struct {
   int32_t kmeans_max_iter; /* (300)                                            */
   uint64_t seed;           /* k-means seed (0)                                 */
   int32_t verbose;         /* print one line per Newton step to stderr (0)     */
+  int32_t hessian_form;    /* PSPEC_HESSIAN_EXACT (default) or _ALG1: the
+                              Euclidean Hessian the subproblems use           */
 } pspec_solve_opts;
 
 typedef struct {

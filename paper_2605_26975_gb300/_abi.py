@@ -26,6 +26,9 @@ PSPEC_F32 = 0
 PSPEC_F64 = 1
 PSPEC_HOST_PTRS = 0x1
 PSPEC_CHECK_SYMMETRY = 0x2
+PSPEC_HVP_ALG1 = 0x4
+PSPEC_HESSIAN_EXACT = 0
+PSPEC_HESSIAN_ALG1 = 1
 
 
 class SolveOpts(C.Structure):
@@ -34,7 +37,7 @@ class SolveOpts(C.Structure):
                 ("delta_bar_scale", C.c_double), ("delta0_scale", C.c_double),
                 ("rho_prime", C.c_double), ("rho_reg", C.c_double),
                 ("kmeans_restarts", C.c_int32), ("kmeans_max_iter", C.c_int32),
-                ("seed", C.c_uint64), ("verbose", C.c_int32)]
+                ("seed", C.c_uint64), ("verbose", C.c_int32), ("hessian_form", C.c_int32)]
 
 
 class SolveStats(C.Structure):

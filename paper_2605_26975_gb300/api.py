@@ -98,14 +98,16 @@ class Graph:
         check(st, "pspec_eval")
         return (F, grad, P) if parts else (F, grad)
 
-    def hvp(self, U, V, p, out=None):
+    def hvp(self, U, V, p, out=None, alg1=False):
+        """Exact Hessian of F_p at U applied to V; alg1=True leaves out the
+        rank-two terms (the sparse-plus-diagonal form of Algorithm 1)."""
         U = _dev_block(U, "U", self.n)
         V = _dev_block(V, "V", self.n)
         if V.shape != U.shape or V.dtype != U.dtype:
             raise ValueError("U and V must have the same shape and dtype")
         HV = torch.empty_like(U) if out is None else out
         st = lib().pspec_hvp(self._h, _ptr(U), _ptr(V), U.shape[1], float(p), _DT[U.dtype],
-                             _ptr(HV), 0, _stream())
+                             _ptr(HV), _abi.PSPEC_HVP_ALG1 if alg1 else 0, _stream())
         check(st, "pspec_hvp")
         return HV
 

@@ -67,6 +67,8 @@ struct EdgeArgs {
   // batches: per-task column sums go to task_part[task][NV] instead of the
   // grid reduction (NULL for a single graph)
   float* task_part;
+  // HVP in Algorithm 1's form: the epilogue's rank-two coefficient is zero
+  int alg1;
 };
 
 template <int K, int CPL, int VW>
@@ -451,7 +453,7 @@ __global__ void __launch_bounds__(kBlock, edge_min_blocks<K, HVP>()) edge_kernel
       if (!isfinite(sN) || !isfinite(sD)) flags |= kStatusNonFinite;
       coef[0 * 16 + c] = p * (p - 1.0) / D;  // A
       coef[1 * 16 + c] = lam;                // lambda
-      coef[2 * 16 + c] = p * p / (D * D);    // B
+      coef[2 * 16 + c] = a.alg1 ? 0.0 : p * p / (D * D);  // B
       coef[3 * 16 + c] = sD;                 // sigma_D
       coef[4 * 16 + c] = sN - 2.0 * lam * sD;
     } else {

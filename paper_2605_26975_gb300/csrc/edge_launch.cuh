@@ -44,6 +44,7 @@ pspec_status launch_edges_k(pspec_graph* g, const EdgeLaunch& L, cudaStream_t s)
   a.status = g->d_status;
   a.skip = L.skip;
   a.task_part = L.task_part;
+  a.alg1 = L.alg1 ? 1 : 0;
   const int want = g->edge_blocks_per_sm[q_index(Q)];
   int blocks = grid_blocks(g, want > 0 ? std::min(want, occ) : occ);
   blocks = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (ts.n_tasks + kWarps - 1) / kWarps));

@@ -485,6 +485,8 @@ void pspec_graph_destroy(pspec_graph* g) {
   cudaFree(g->d_task_part);
   cudaFree(g->d_scratch);
   cudaFree(g->d_hub_part);
+  if (g->solve_stream) cudaStreamDestroy(g->solve_stream);
+  if (g->solve_event) cudaEventDestroy(g->solve_event);
   cudaFree(g->d_block_part);
   cudaFree(g->d_group_part);
   cudaFree(g->d_counters);

@@ -103,6 +103,11 @@ struct pspec_graph {
   // solver workspace (allocated on first solve)
   void* d_solve = nullptr;
   size_t d_solve_bytes = 0;
+  // pspec_solve runs on this private stream (joined to the caller's stream
+  // by events), on which it can capture CUDA graphs whatever the caller's
+  // stream is (capture is not possible on the legacy default stream)
+  cudaStream_t solve_stream = nullptr;
+  cudaEvent_t solve_event = nullptr;
   pspec::Timing timing;
 };
 
@@ -158,6 +163,7 @@ struct EdgeLaunch {
   int k;
   const int* skip = nullptr;  // device flag: when nonzero the launch does nothing
   float* task_part = nullptr; // batches: per-task column sums (see edge_kernels.cuh)
+  bool alg1 = false;          // HVP: Algorithm 1's form (no rank-two terms)
 };
 pspec_status edge_occupancy(int k, bool hvp, int* blocks_per_sm);
 pspec_status launch_eval_edges(pspec_graph* g, const EdgeLaunch& a, cudaStream_t s);
@@ -167,13 +173,13 @@ pspec_status launch_hvp_edges(pspec_graph* g, const EdgeLaunch& a, cudaStream_t 
 pspec_status eval_plain64(pspec_graph* g, const double* U, int k, double p, double* F_out,
                           double* grad, double* parts, cudaStream_t s);
 pspec_status hvp_plain64(pspec_graph* g, const double* U, const double* V, int k, double p,
-                         double* HV, cudaStream_t s);
+                         double* HV, cudaStream_t s, bool alg1 = false);
 
 // FP32 fast path, device pointers only
 pspec_status eval_fast(pspec_graph* g, const float* U, int k, double p, double* F_out,
                        float* grad, double* parts, cudaStream_t s);
 pspec_status hvp_fast(pspec_graph* g, const float* U, const float* V, int k, double p, float* HV,
-                      cudaStream_t s, const int* skip = nullptr);
+                      cudaStream_t s, const int* skip = nullptr, bool alg1 = false);
 
 // batches: per-graph scalars, 128 doubles per graph in d_graph_scalars
 constexpr int kGsN = 0, kGsD = 16, kGsC0 = 32, kGsC1 = 48, kGsC2 = 64, kGsC3 = 80, kGsC4 = 96,
@@ -181,7 +187,7 @@ constexpr int kGsN = 0, kGsD = 16, kGsC0 = 32, kGsC1 = 48, kGsC2 = 64, kGsC3 = 8
 pspec_status eval_batched(pspec_graph* g, const float* U, int k, double p, double* F_out,
                           float* grad, double* parts, cudaStream_t s);
 pspec_status hvp_batched(pspec_graph* g, const float* U, const float* V, int k, double p,
-                         float* HV, cudaStream_t s);
+                         float* HV, cudaStream_t s, bool alg1 = false);
 int64_t task_count(pspec_graph* g, int k);
 
 // scalar slots in d_scalars

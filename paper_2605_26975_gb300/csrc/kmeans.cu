@@ -86,55 +86,158 @@ __global__ void __launch_bounds__(kKmBlock) km_seed_dist(const T* X, int64_t n, 
   if (threadIdx.x == 0) block_sum[blockIdx.x] = s[0];
 }
 
-// one thread: first index whose running D^2 sum exceeds u * total
-__global__ void km_pick(const double* d2, const double* block_sum, int nblocks, int64_t n, double u,
-                        int64_t* out_idx) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double total = 0.0;
-  for (int b = 0; b < nblocks; ++b) total += block_sum[b];
-  int64_t idx;
-  if (total > 0.0) {
-    const double target = u * total;
-    const int64_t per = (n + nblocks - 1) / nblocks;
-    double run = 0.0;
-    int b = 0;
-    while (b < nblocks - 1 && run + block_sum[b] <= target) run += block_sum[b++];
-    // walk on from that block's start; the walk may run past the block when
-    // the block's tree sum and the running sum round differently
-    const int64_t i0 = b * per;
-    idx = n - 1;
-    for (int64_t i = i0; i < n; ++i) {
-      run += d2[i];
-      if (run > target) { idx = i; break; }
+// first index whose running D^2 sum exceeds u * total (one block of
+// kKmBlock threads).  Thread 0 runs over the block sums to the block the
+// target falls in; from that block's first row the walk goes on in windows of
+// kKmBlock chunks of kPickChunk rows: the threads sum their chunks, thread 0
+// adds the chunk sums in order and walks the one chunk the target falls in
+// row by row.
+constexpr int kPickChunk = 32;
+
+__global__ void __launch_bounds__(kKmBlock) km_pick(const double* d2, const double* block_sum,
+                                                    int nblocks, int64_t n, double u,
+                                                    int64_t* out_idx) {
+  __shared__ double csum[kKmBlock];
+  __shared__ double s_run, s_target;
+  __shared__ int64_t s_i0, s_found;
+  const int t = threadIdx.x;
+  if (t == 0) {
+    double total = 0.0;
+    for (int b = 0; b < nblocks; ++b) total += block_sum[b];
+    s_found = -1;
+    if (total > 0.0) {
+      const double target = u * total;
+      const int64_t per = (n + nblocks - 1) / nblocks;
+      double run = 0.0;
+      int b = 0;
+      while (b < nblocks - 1 && run + block_sum[b] <= target) run += block_sum[b++];
+      s_run = run;
+      s_target = target;
+      s_i0 = (int64_t)b * per;
+    } else {
+      s_found = min((int64_t)(u * (double)n), n - 1);
     }
-  } else {
-    idx = min((int64_t)(u * (double)n), n - 1);
   }
-  *out_idx = idx;
+  __syncthreads();
+  if (s_found >= 0) {
+    if (t == 0) *out_idx = s_found;
+    return;
+  }
+  // the walk may run past the block when the block's tree sum and the
+  // running sum round differently
+  for (int64_t w0 = s_i0; w0 < n; w0 += (int64_t)kKmBlock * kPickChunk) {
+    const int64_t c0 = w0 + (int64_t)t * kPickChunk;
+    double cs = 0.0;
+    for (int q = 0; q < kPickChunk; ++q)
+      if (c0 + q < n) cs += d2[c0 + q];
+    csum[t] = cs;
+    __syncthreads();
+    if (t == 0) {
+      double run = s_run;
+      for (int c = 0; c < kKmBlock && s_found < 0; ++c) {
+        const int64_t r0 = w0 + (int64_t)c * kPickChunk;
+        if (r0 >= n) break;
+        if (run + csum[c] > s_target) {  // the target is in this chunk: walk it
+          // (when rounding says otherwise, the walk goes on in the next chunk)
+          for (int q = 0; q < kPickChunk && r0 + q < n; ++q) {
+            run += d2[r0 + q];
+            if (run > s_target) {
+              s_found = r0 + q;
+              break;
+            }
+          }
+        } else {
+          run += csum[c];
+        }
+      }
+      s_run = run;
+    }
+    __syncthreads();
+    if (s_found >= 0) break;
+  }
+  if (t == 0) *out_idx = s_found >= 0 ? s_found : n - 1;
 }
 
 // labels[i] = argmin_c dist(X_i, mu_c); dmin[i] = that distance; count changes
+//
+// The decision is the FP64 one (each subtraction, product and sum rounded
+// once, ties to the smaller centre).  For FP32 rows it is screened in FP32:
+// with u = 2^-24, t_j = fl32(x_j - fl32(mu_j)) differs from a_j = x_j - mu_j by
+// at most u'(|a_j| + |mu_j|), u' = u(1+u), and the FP32 sum of the t_j^2 from
+// sum a_j^2 by at most
+//   (2u' + u + gamma_{dim-1}(1+u) + 2u'^2) d + 2u' |mu| sqrt(d) + 2u'^2 |mu|^2
+// (Cauchy-Schwarz on sum |a_j||mu_j|), while the FP64 distance is within
+// (dim+2) 2^-53 d of sum a_j^2.  E(c) below is twice the sum of both bounds
+// (the factor covers using the computed d32 for d).  When the FP32 winner's
+// d32 + E stays below every other centre's d32 - E, the FP64 decision is the
+// same centre, and only its FP64 distance is computed; a row that is too
+// close to call runs the full FP64 loop.
+template <typename T>
+__device__ __forceinline__ double km_dist64(const T* xr, const double* mu, int dim) {
+  double acc = 0.0;
+  for (int j = 0; j < dim; ++j) {
+    const double t = __dsub_rn((double)xr[j], mu[j]);
+    acc = __dadd_rn(acc, __dmul_rn(t, t));
+  }
+  return acc;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kKmBlock) km_assign(const T* X, int64_t n, int dim, int C,
                                                       const double* centers, int32_t* labels,
                                                       double* dmin, unsigned* changed) {
   __shared__ double mu[kKmMaxC * kKmMaxDim];
-  for (int t = threadIdx.x; t < C * dim; t += blockDim.x) mu[t] = centers[t];
+  __shared__ float mu32[kKmMaxC * kKmMaxDim];
+  __shared__ float nmu[kKmMaxC];  // |mu_c|, rounded up
+  for (int t = threadIdx.x; t < C * dim; t += blockDim.x) {
+    mu[t] = centers[t];
+    mu32[t] = (float)centers[t];
+  }
   __syncthreads();
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    double q = 0.0;
+    for (int j = 0; j < dim; ++j) q += mu[c * dim + j] * mu[c * dim + j];
+    nmu[c] = (float)(sqrt(q) * (1.0 + 1e-6));
+  }
+  __syncthreads();
+  constexpr float u = 5.9604645e-8f;  // 2^-24
+  const float k_rel = 2.0f * u * (float)(dim + 3) + 2.0f * (float)(dim + 2) * 1.1102230e-16f;
   unsigned local = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    double xr[kKmMaxDim];
-    for (int j = 0; j < dim; ++j) xr[j] = (double)X[i * dim + j];
-    double best = 0.0;
-    int arg = 0;
-    for (int c = 0; c < C; ++c) {
-      double acc = 0.0;
-      for (int j = 0; j < dim; ++j) {
-        const double t = __dsub_rn(xr[j], mu[c * dim + j]);
-        acc = __dadd_rn(acc, __dmul_rn(t, t));
+    T xr[kKmMaxDim];
+    for (int j = 0; j < dim; ++j) xr[j] = X[i * dim + j];
+    int arg = -1;
+    if constexpr (sizeof(T) == 4) {
+      float best_hi = 0.f, best_d = 0.f;  // winner's d32 + E and d32
+      int c1 = 0;
+      float lo1 = 3.4e38f, lo2 = 3.4e38f;  // two smallest d32 - E ...
+      int lo1c = -1;                       // ... and the centre of the smallest
+      for (int c = 0; c < C; ++c) {
+        float d = 0.f;
+        for (int j = 0; j < dim; ++j) {
+          const float t = xr[j] - mu32[c * dim + j];
+          d = fmaf(t, t, d);
+        }
+        const float e = 2.0f * (k_rel * d + 2.1f * u * nmu[c] * sqrtf(d) + 3.0f * u * u * nmu[c] * nmu[c]);
+        if (c == 0 || d < best_d) { best_d = d; best_hi = d + e; c1 = c; }
+        const float lo = d - e;
+        if (lo < lo1) { lo2 = lo1; lo1 = lo; lo1c = c; }
+        else if (lo < lo2) lo2 = lo;
       }
-      if (c == 0 || acc < best) { best = acc; arg = c; }
+      const float others_lo = (lo1c == c1) ? lo2 : lo1;
+      if (best_hi < others_lo) arg = c1;  // separated: the FP64 decision is c1
+    }
+    double best;
+    if (arg >= 0) {
+      best = km_dist64(xr, mu + arg * dim, dim);
+    } else {
+      best = 0.0;
+      arg = 0;
+      for (int c = 0; c < C; ++c) {
+        const double acc = km_dist64(xr, mu + c * dim, dim);
+        if (c == 0 || acc < best) { best = acc; arg = c; }
+      }
     }
     if (labels[i] != arg) ++local;
     labels[i] = arg;
@@ -285,7 +388,7 @@ static pspec_status kmeans_impl(const T* X, int64_t n, int dim, int C, uint64_t 
       km_seed_dist<T><<<w.nblocks, kKmBlock, 0, s>>>(X, n, dim, w.centers, 0, 1, w.d2, w.part);
       for (int c = 1; c < C; ++c) {
         const double uc = rng.uniform();
-        km_pick<<<1, 1, 0, s>>>(w.d2, w.part, w.nblocks, n, uc, w.idx);
+        km_pick<<<1, kKmBlock, 0, s>>>(w.d2, w.part, w.nblocks, n, uc, w.idx);
         int64_t idx = 0;
         cudaMemcpyAsync(&idx, w.idx, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
         cudaError_t e = cudaStreamSynchronize(s);

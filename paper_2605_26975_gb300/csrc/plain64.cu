@@ -101,6 +101,7 @@ struct PlainArgs {
   int k;
   int l;
   double p;
+  int alg1;  // HVP in Algorithm 1's form: no rank-two coefficient
   GridReduce64 gr;
   double* scalars;
   int* status;
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(kPlainBlock) plain_col_kernel(PlainArgs a) {
       sc[kSlotCD + l] = s_tot[3];
       coef[0 * 16 + l] = p * (p - 1.0) / D;
       coef[1 * 16 + l] = lam;
-      coef[2 * 16 + l] = p * p / (D * D);
+      coef[2 * 16 + l] = a.alg1 ? 0.0 : p * p / (D * D);
       coef[3 * 16 + l] = s_tot[3];
       coef[4 * 16 + l] = s_tot[2] - 2.0 * lam * s_tot[3];
     } else {
@@ -207,6 +208,7 @@ static PlainArgs plain_args(pspec_graph* g, const double* U, const double* V, do
   a.k = k;
   a.l = 0;
   a.p = p;
+  a.alg1 = 0;
   a.gr.block_part = g->d_red64;
   a.gr.group_part = g->d_red64 + (size_t)g->max_blocks * 64;
   a.gr.counters = g->d_counters;
@@ -245,7 +247,7 @@ pspec_status eval_plain64(pspec_graph* g, const double* U, int k, double p, doub
 }
 
 pspec_status hvp_plain64(pspec_graph* g, const double* U, const double* V, int k, double p,
-                         double* HV, cudaStream_t s) {
+                         double* HV, cudaStream_t s, bool alg1) {
   const size_t need = (size_t)g->n * k * 2;  // doubles stored in the float scratch
   if (g->scratch_elems < need) {
     if (g->d_scratch) cudaFree(g->d_scratch);
@@ -256,6 +258,7 @@ pspec_status hvp_plain64(pspec_graph* g, const double* U, const double* V, int k
   }
   double* Dl = reinterpret_cast<double*>(g->d_scratch);
   PlainArgs a = plain_args(g, U, V, HV, Dl, k, p);
+  a.alg1 = alg1 ? 1 : 0;
   const int blocks = plain_blocks(g);
   for (int l = 0; l < k; ++l) {
     a.l = l;

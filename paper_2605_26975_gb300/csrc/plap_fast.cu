@@ -175,10 +175,11 @@ static pspec_status ensure_scratch(pspec_graph* g, size_t elems) {
 }
 
 pspec_status hvp_fast(pspec_graph* g, const float* U, const float* V, int k, double p, float* HV,
-                      cudaStream_t s, const int* skip) {
+                      cudaStream_t s, const int* skip, bool alg1) {
   const int64_t ne = g->n * k;
   PSPEC_TRY(ensure_scratch(g, (size_t)ne));
   EdgeLaunch L{U, V, HV, g->d_scratch, (float)p, k, skip};
+  L.alg1 = alg1;
   PSPEC_TRY(launch_hvp_edges(g, L, s));
   const float pm2 = (float)p - 2.0f;
   TimedScope timer(g, "hvp_epilogue", s);
@@ -199,7 +200,8 @@ pspec_status hvp_fast(pspec_graph* g, const float* U, const float* V, int k, dou
 // coefficients written to gs[graph].
 __global__ void __launch_bounds__(256) batch_reduce(const float* __restrict__ part,
                                                     const int32_t* __restrict__ graph_task, int K,
-                                                    int NQ, double p, double* gs, int* status) {
+                                                    int NQ, double p, bool alg1, double* gs,
+                                                    int* status) {
   __shared__ float2 s_part[256];
   __shared__ double s_tot[64];
   const int G = blockIdx.x;
@@ -209,8 +211,18 @@ __global__ void __launch_bounds__(256) batch_reduce(const float* __restrict__ pa
   const int t0 = graph_task[G], t1 = graph_task[G + 1];
   Kahan acc;
   acc.init();
-  if (j < parts)
-    for (int t = t0 + j; t < t1; t += parts) acc.add(part[(size_t)t * NV + v]);
+  if (j < parts) {
+    // eight slots' loads in flight at a time, added in slot order
+    int t = t0 + j;
+    for (; t + 7 * parts < t1; t += 8 * parts) {
+      float x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) x[u] = __ldg(&part[(size_t)(t + u * parts) * NV + v]);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc.add(x[u]);
+    }
+    for (; t < t1; t += parts) acc.add(part[(size_t)t * NV + v]);
+  }
   s_part[threadIdx.x] = kahan_to_ff(acc);
   __syncthreads();
   if (threadIdx.x < NV) {
@@ -233,7 +245,7 @@ __global__ void __launch_bounds__(256) batch_reduce(const float* __restrict__ pa
       const double sN = s_tot[2 * K + c], sD = s_tot[3 * K + c];
       g[kGsC0 + c] = p * (p - 1.0) / D;
       g[kGsC1 + c] = lam;
-      g[kGsC2 + c] = p * p / (D * D);
+      g[kGsC2 + c] = alg1 ? 0.0 : p * p / (D * D);
       g[kGsC3 + c] = sD;
       g[kGsC4 + c] = sN - 2.0 * lam * sD;
     } else {
@@ -336,8 +348,8 @@ pspec_status eval_batched(pspec_graph* g, const float* U, int k, double p, doubl
   const int G = g->n_graphs;
   {
     TimedScope timer(g, "batch_reduce", s);
-    batch_reduce<<<G, 256, 0, s>>>(g->d_task_part, graph_task_of(g, k), k, 2, p, g->d_graph_scalars,
-                                   g->d_status);
+    batch_reduce<<<G, 256, 0, s>>>(g->d_task_part, graph_task_of(g, k), k, 2, p, false,
+                                   g->d_graph_scalars, g->d_status);
     PSPEC_CUDA(cudaGetLastError());
   }
   const int64_t ne = g->n * k;
@@ -366,7 +378,7 @@ pspec_status eval_batched(pspec_graph* g, const float* U, int k, double p, doubl
 }
 
 pspec_status hvp_batched(pspec_graph* g, const float* U, const float* V, int k, double p, float* HV,
-                         cudaStream_t s) {
+                         cudaStream_t s, bool alg1) {
   const int64_t ne = g->n * k;
   PSPEC_TRY(ensure_scratch(g, (size_t)ne));
   PSPEC_TRY(ensure_task_part(g, k));
@@ -374,7 +386,7 @@ pspec_status hvp_batched(pspec_graph* g, const float* U, const float* V, int k, 
   PSPEC_TRY(launch_hvp_edges(g, L, s));
   {
     TimedScope timer(g, "batch_reduce", s);
-    batch_reduce<<<g->n_graphs, 256, 0, s>>>(g->d_task_part, graph_task_of(g, k), k, 4, p,
+    batch_reduce<<<g->n_graphs, 256, 0, s>>>(g->d_task_part, graph_task_of(g, k), k, 4, p, alg1,
                                              g->d_graph_scalars, g->d_status);
     PSPEC_CUDA(cudaGetLastError());
   }
@@ -469,12 +481,13 @@ extern "C" pspec_status pspec_hvp(pspec_graph* g, const void* U, const void* V, 
     PSPEC_TRY(check_block(HV_out, k, dtype, "HV_out"));
     if (HV_out == U || HV_out == V) return set_error(PSPEC_ERR_INVALID_ARG, "HV_out aliases an input");
   }
+  const bool alg1 = (flags & PSPEC_HVP_ALG1) != 0;
   if (g->n_graphs > 1)
-    PSPEC_TRY(hvp_batched(g, (const float*)dU, (const float*)dV, k, p, (float*)dH, s));
+    PSPEC_TRY(hvp_batched(g, (const float*)dU, (const float*)dV, k, p, (float*)dH, s, alg1));
   else if (dtype == PSPEC_F32)
-    PSPEC_TRY(hvp_fast(g, (const float*)dU, (const float*)dV, k, p, (float*)dH, s));
+    PSPEC_TRY(hvp_fast(g, (const float*)dU, (const float*)dV, k, p, (float*)dH, s, nullptr, alg1));
   else
-    PSPEC_TRY(hvp_plain64(g, (const double*)dU, (const double*)dV, k, p, (double*)dH, s));
+    PSPEC_TRY(hvp_plain64(g, (const double*)dU, (const double*)dV, k, p, (double*)dH, s, alg1));
   if (flags & PSPEC_HOST_PTRS) {
     PSPEC_CUDA(cudaMemcpyAsync(HV_out, dH, bytes, cudaMemcpyDeviceToHost, s));
     return take_status(g, s);

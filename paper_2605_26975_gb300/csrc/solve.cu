@@ -23,6 +23,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 
 #include "internal.h"
 #include "solve_kernels.cuh"
@@ -38,7 +39,7 @@ struct SolveWork {
   TcgState* st;
   int* bad;
   GridRed gr;
-  int vblocks, gblocks;
+  int vblocks, gblocks, rblocks;  // elementwise, Gram, row kernels
 };
 
 template <typename T>
@@ -46,7 +47,10 @@ pspec_status carve(pspec_graph* g, int k, SolveWork<T>* w) {
   const size_t m = (size_t)g->n * k;
   const size_t vec = ((sizeof(T) * m + 255) / 256) * 256;
   w->vblocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * 4, ((int64_t)m + kSolveBlock - 1) / kSolveBlock));
-  w->gblocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * 2, (g->n + 7) / 8));
+  w->gblocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * 8,
+                                                           (g->n + kGramTile - 1) / kGramTile));
+  w->rblocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * 4,
+                                                           (g->n + kSolveBlock - 1) / kSolveBlock));
   const int maxb = std::max(w->vblocks, w->gblocks);
   const int groups = (maxb + kGroup - 1) / kGroup;
   const size_t red = sizeof(double) * 256 * (size_t)(maxb + groups);
@@ -82,6 +86,45 @@ pspec_status carve(pspec_graph* g, int k, SolveWork<T>* w) {
   return PSPEC_OK;
 }
 
+// CUDA graphs of a chunk of CG iterations, one per (iterate buffer, p): the
+// solve alternates between two iterate buffers, so a stage needs at most two.
+struct GraphCache {
+  bool enabled = true;
+  struct Entry {
+    const void* U;
+    double p;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Entry> entries;
+  template <typename F>
+  pspec_status get(const void* U, double p, cudaStream_t s, F&& body, cudaGraphExec_t* out) {
+    for (const Entry& e : entries)
+      if (e.U == U && e.p == p) {
+        *out = e.exec;
+        return PSPEC_OK;
+      }
+    PSPEC_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    pspec_status st = body();
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (st != PSPEC_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture(tCG chunk)");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGraphInstantiate(tCG chunk)");
+    entries.push_back({U, p, exec});
+    *out = exec;
+    return PSPEC_OK;
+  }
+  ~GraphCache() {
+    for (const Entry& e : entries) cudaGraphExecDestroy(e.exec);
+  }
+};
+
 template <typename T>
 struct Solver {
   pspec_graph* g;
@@ -98,11 +141,12 @@ struct Solver {
     else
       return eval_plain64(g, U, k, p, w.F, grad, nullptr, s);
   }
+  bool alg1 = false;  // Algorithm 1's Hessian form instead of the exact one
   pspec_status hvp(const T* U, const T* V, double p, T* out, const int* skip) {
     if constexpr (sizeof(T) == 4)
-      return hvp_fast(g, U, V, k, p, out, s, skip);
+      return hvp_fast(g, U, V, k, p, out, s, skip, alg1);
     else
-      return hvp_plain64(g, U, V, k, p, out, s);
+      return hvp_plain64(g, U, V, k, p, out, s, alg1);
   }
   pspec_status gram(const T* A, const T* B, double* G, const int* done = nullptr) {
     TimedScope timer(g, "solve_gram", s);
@@ -119,18 +163,36 @@ struct Solver {
   pspec_status combine(T* out, const T* X, double a, const T* Y, double b, const T* P,
                        const double* M1, const T* Q, const double* M2) {
     TimedScope timer(g, "solve_combine", s);
-    combine_kernel<T><<<w.vblocks, kSolveBlock, 0, s>>>(out, X, a, Y, b, P, M1, Q, M2, n, k, nullptr);
+    switch (k_bucket(k)) {
+      case 4: combine_kernel<T, 4><<<w.rblocks, kSolveBlock, 0, s>>>(out, X, a, Y, b, P, M1, Q, M2, n, k, nullptr); break;
+      case 8: combine_kernel<T, 8><<<w.rblocks, kSolveBlock, 0, s>>>(out, X, a, Y, b, P, M1, Q, M2, n, k, nullptr); break;
+      default: combine_kernel<T, 16><<<w.rblocks, kSolveBlock, 0, s>>>(out, X, a, Y, b, P, M1, Q, M2, n, k, nullptr);
+    }
     PSPEC_CUDA(cudaGetLastError());
     return PSPEC_OK;
+  }
+  void rmul(T* out, const T* A) {
+    switch (k_bucket(k)) {
+      case 4: rmul_kernel<T, 4><<<w.rblocks, kSolveBlock, 0, s>>>(out, A, w.Rinv, n, k); break;
+      case 8: rmul_kernel<T, 8><<<w.rblocks, kSolveBlock, 0, s>>>(out, A, w.Rinv, n, k); break;
+      default: rmul_kernel<T, 16><<<w.rblocks, kSolveBlock, 0, s>>>(out, A, w.Rinv, n, k);
+    }
+  }
+  void hess(TcgState* st) {
+    switch (k_bucket(k)) {
+      case 4: hess_kernel<T, 4><<<w.rblocks, kSolveBlock, 0, s>>>(w.Hd, w.He, w.U, w.G, w.delta, w.M, n, k, st, w.gr); break;
+      case 8: hess_kernel<T, 8><<<w.rblocks, kSolveBlock, 0, s>>>(w.Hd, w.He, w.U, w.G, w.delta, w.M, n, k, st, w.gr); break;
+      default: hess_kernel<T, 16><<<w.rblocks, kSolveBlock, 0, s>>>(w.Hd, w.He, w.U, w.G, w.delta, w.M, n, k, st, w.gr);
+    }
   }
   // out = qf(A) by Cholesky-QR twice; A is overwritten
   pspec_status qf(T* A, T* out) {
     PSPEC_TRY(gram(A, A, w.Gram));
     chol_inv_kernel<<<1, 1, 0, s>>>(w.Gram, k, w.Rinv, w.bad);
-    rmul_kernel<T><<<w.vblocks, kSolveBlock, 0, s>>>(out, A, w.Rinv, n, k);
+    rmul(out, A);
     PSPEC_TRY(gram(out, out, w.Gram));
     chol_inv_kernel<<<1, 1, 0, s>>>(w.Gram, k, w.Rinv, w.bad);
-    rmul_kernel<T><<<w.vblocks, kSolveBlock, 0, s>>>(A, out, w.Rinv, n, k);
+    rmul(A, out);
     PSPEC_CUDA(cudaMemcpyAsync(out, A, sizeof(T) * m, cudaMemcpyDeviceToDevice, s));
     PSPEC_CUDA(cudaGetLastError());
     return PSPEC_OK;
@@ -170,12 +232,15 @@ static pspec_status solve_impl(pspec_graph* g, int k, const double* sched, int n
   S.n = g->n;
   S.m = g->n * k;
   S.s = s;
+  S.alg1 = o.hessian_form == PSPEC_HESSIAN_ALG1;
   PSPEC_TRY(carve<T>(g, k, &S.w));
   SolveWork<T>& w = S.w;
   const int64_t m = S.m;
   PSPEC_CUDA(cudaMemcpyAsync(w.U, U_io, sizeof(T) * m, cudaMemcpyDeviceToDevice, s));
   PSPEC_CUDA(cudaMemsetAsync(w.bad, 0, sizeof(int), s));
-  const int chunk = sizeof(T) == 4 ? 4 : 1;  // CG iterations per host check
+  const int chunk = sizeof(T) == 4 ? 6 : 2;  // CG iterations per host check
+  GraphCache graphs;
+  graphs.enabled = !g->timing.enabled;  // per-kernel timing needs eager launches
   pspec_solve_stats st_local;
   std::memset(&st_local, 0, sizeof(st_local));
   bool all_converged = true;
@@ -214,20 +279,32 @@ static pspec_status solve_impl(pspec_graph* g, int k, const double* sched, int n
       PSPEC_CUDA(cudaMemcpyAsync(w.r, w.rg, sizeof(T) * m, cudaMemcpyDeviceToDevice, s));
       PSPEC_TRY(S.combine(w.delta, w.rg, -1.0, nullptr, 0.0, nullptr, nullptr, nullptr, nullptr));
       const int* done = &w.st->done;
-      TcgState hs{};
-      for (int it = 0; it < o.max_inner; it += chunk) {
-        for (int c = 0; c < chunk && it + c < o.max_inner; ++c) {
+      // one CG iteration: Hessian product, U^T (H delta), the Riemannian
+      // Hessian and the CG updates, all decided on the device
+      auto cg_iters = [&](int count) -> pspec_status {
+        for (int c = 0; c < count; ++c) {
           PSPEC_TRY(S.hvp(w.U, w.delta, p, w.He, done));
           PSPEC_TRY(S.gram(w.U, w.He, w.G, done));
-          {
-            TimedScope timer(g, "solve_tcg_vec", s);
-            hess_kernel<T><<<w.vblocks, kSolveBlock, 0, s>>>(w.Hd, w.He, w.U, w.G, w.delta, w.M,
-                                                              S.n, k, w.st, w.gr);
-            cg_update_kernel<T><<<w.vblocks, kSolveBlock, 0, s>>>(w.eta, w.Heta, w.r, w.delta,
-                                                                   w.Hd, m, w.st, w.gr);
-            direction_kernel<T><<<w.vblocks, kSolveBlock, 0, s>>>(w.delta, w.r, m, w.st);
-            PSPEC_CUDA(cudaGetLastError());
-          }
+          TimedScope timer(g, "solve_tcg_vec", s);
+          S.hess(w.st);
+          cg_update_kernel<T><<<w.vblocks, kSolveBlock, 0, s>>>(w.eta, w.Heta, w.r, w.delta,
+                                                                 w.Hd, m, w.st, w.gr);
+          direction_kernel<T><<<w.vblocks, kSolveBlock, 0, s>>>(w.delta, w.r, m, w.st);
+          PSPEC_CUDA(cudaGetLastError());
+        }
+        return PSPEC_OK;
+      };
+      TcgState hs{};
+      for (int it = 0; it < o.max_inner; it += chunk) {
+        // after the first chunk of a stage (which builds every lazily
+        // allocated buffer), chunks replay a CUDA graph of `chunk` iterations
+        // per (iterate buffer, p); iterations past the stop are no-ops
+        if (graphs.enabled && (outer > 1 || it > 0)) {
+          cudaGraphExec_t exec = nullptr;
+          PSPEC_TRY(graphs.get(w.U, p, s, [&]() { return cg_iters(chunk); }, &exec));
+          PSPEC_CUDA(cudaGraphLaunch(exec, s));
+        } else {
+          PSPEC_TRY(cg_iters(std::min(chunk, o.max_inner - it)));
         }
         PSPEC_CUDA(cudaMemcpyAsync(&hs, w.st, sizeof(TcgState), cudaMemcpyDeviceToHost, s));
         PSPEC_CUDA(cudaStreamSynchronize(s));
@@ -330,6 +407,7 @@ extern "C" void pspec_solve_opts_default(pspec_solve_opts* o) {
   o->kmeans_max_iter = 300;
   o->seed = 0;
   o->verbose = 0;
+  o->hessian_form = PSPEC_HESSIAN_EXACT;
 }
 
 extern "C" pspec_status pspec_solve(pspec_graph* g, int k, const double* p_schedule, int n_p,
@@ -352,11 +430,24 @@ extern "C" pspec_status pspec_solve(pspec_graph* g, int k, const double* p_sched
   if (opts) o = *opts;
   if (o.max_inner < 1 || o.max_outer < 0 || o.kmeans_restarts < 1)
     return set_error(PSPEC_ERR_INVALID_ARG, "bad iteration caps");
+  if (o.hessian_form != PSPEC_HESSIAN_EXACT && o.hessian_form != PSPEC_HESSIAN_ALG1)
+    return set_error(PSPEC_ERR_INVALID_ARG, "hessian_form must be PSPEC_HESSIAN_EXACT or PSPEC_HESSIAN_ALG1");
   PSPEC_TRY(check_block(U_inout, k, dtype, "U_inout"));
-  cudaStream_t s = (cudaStream_t)stream;
-  if (dtype == PSPEC_F32)
-    return solve_impl<float>(g, k, p_schedule, n_p, o, (float*)U_inout, labels_out, rcut_out, stats, s);
-  if (dtype == PSPEC_F64)
-    return solve_impl<double>(g, k, p_schedule, n_p, o, (double*)U_inout, labels_out, rcut_out, stats, s);
-  return set_error(PSPEC_ERR_INVALID_ARG, "bad dtype");
+  if (dtype != PSPEC_F32 && dtype != PSPEC_F64) return set_error(PSPEC_ERR_INVALID_ARG, "bad dtype");
+  cudaStream_t caller = (cudaStream_t)stream;
+  if (!g->solve_stream) {
+    PSPEC_CUDA(cudaStreamCreateWithFlags(&g->solve_stream, cudaStreamNonBlocking));
+    PSPEC_CUDA(cudaEventCreateWithFlags(&g->solve_event, cudaEventDisableTiming));
+  }
+  cudaStream_t s = g->solve_stream;
+  PSPEC_CUDA(cudaEventRecord(g->solve_event, caller));  // the caller's earlier work first
+  PSPEC_CUDA(cudaStreamWaitEvent(s, g->solve_event, 0));
+  const pspec_status st =
+      dtype == PSPEC_F32
+          ? solve_impl<float>(g, k, p_schedule, n_p, o, (float*)U_inout, labels_out, rcut_out, stats, s)
+          : solve_impl<double>(g, k, p_schedule, n_p, o, (double*)U_inout, labels_out, rcut_out, stats, s);
+  // whatever the solve left enqueued comes before the caller's later work
+  cudaEventRecord(g->solve_event, s);
+  cudaStreamWaitEvent(caller, g->solve_event, 0);
+  return st;
 }

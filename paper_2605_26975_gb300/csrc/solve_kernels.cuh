@@ -59,6 +59,26 @@ __device__ __forceinline__ double red_to_double(double a) { return a; }
 __device__ __forceinline__ float2 red_shfl(float2 v, int off) { return shfl_xor_ff(v, off); }
 __device__ __forceinline__ double red_shfl(double v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
 
+// 16-byte vectors of T for the elementwise loops (all blocks are carved at
+// 256-byte boundaries, so element 0 of every block is 16-byte aligned)
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+  static constexpr int W = 4;
+  using type = float4;
+  __device__ static float get(const float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+  __device__ static void set(float4& v, int i, float x) {
+    if (i == 0) v.x = x; else if (i == 1) v.y = x; else if (i == 2) v.z = x; else v.w = x;
+  }
+};
+template <> struct Vec16<double> {
+  static constexpr int W = 2;
+  using type = double2;
+  __device__ static double get(const double2& v, int i) { return i == 0 ? v.x : v.y; }
+  __device__ static void set(double2& v, int i, double x) {
+    if (i == 0) v.x = x; else v.y = x;
+  }
+};
+
 struct GridRed {
   void* block_part;
   void* group_part;
@@ -131,8 +151,15 @@ __device__ void block_sum(R (&v)[ND], R* out /* shared [ND] */) {
 }
 
 // ----------------------------------------------------------------- gram ---
-// G[a][b] = sum_i A_ia B_ib  (k x k, FP64 out).  A warp takes a row at a
-// time; lane l owns the pairs (a, b) with a*k + b = l (mod 32).
+// G[a][b] = sum_i A_ia B_ib  (k x k, FP64 out).  A block stages tiles of
+// kGramTile consecutive rows of A and B in shared memory (one coalesced copy
+// of tile*k contiguous values each); thread t owns the pair p = t mod k^2 and
+// the rows r = t div k^2 (mod 256 div k^2) of every tile, so all 256 threads
+// work for any k.  A thread's share of a tile (at most 128 products) is
+// summed with FMAs and added to its compensated running sum; then the row
+// groups in order, then the grid.
+constexpr int kGramTile = 128;
+
 template <typename T>
 __global__ void __launch_bounds__(kSolveBlock) gram_kernel(const T* __restrict__ A,
                                                            const T* __restrict__ B, int64_t n,
@@ -140,44 +167,109 @@ __global__ void __launch_bounds__(kSolveBlock) gram_kernel(const T* __restrict__
                                                            const int* done) {
   using R = typename RedT<T>::type;
   if (done && *done) return;
-  __shared__ R s_w[kSolveBlock / 32][kMaxK * kMaxK];
+  __shared__ __align__(16) T sa[kGramTile * kMaxK];
+  __shared__ __align__(16) T sb[kGramTile * kMaxK];
+  __shared__ R s_part[kSolveBlock];
   __shared__ R s_blk[kMaxK * kMaxK];
   __shared__ R s_tot[kMaxK * kMaxK];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int nv = k * k;
-  const int npl = (nv + 31) / 32;  // pairs per lane (<= 8)
-  Acc<T> acc[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) acc[q].init();
-  const int64_t nw = (int64_t)gridDim.x * (kSolveBlock / 32);
-  for (int64_t i = (blockIdx.x * (int64_t)kSolveBlock + threadIdx.x) >> 5; i < n; i += nw) {
-    const T av = lane < k ? A[i * k + lane] : T(0);
-    const T bv = (lane >= 16 && lane - 16 < k) ? B[i * k + lane - 16] : T(0);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      if (q < npl) {
-        const int pr = lane + 32 * q;
-        const int a = pr / k, b = pr % k;
-        const T x = __shfl_sync(0xffffffffu, av, pr < nv ? a : 0);
-        const T y = __shfl_sync(0xffffffffu, bv, pr < nv ? 16 + b : 16);
-        if (pr < nv) acc[q].add(x * y);
+  const int groups = kSolveBlock / nv;  // row groups (>= 1 since k <= 16)
+  const int t = threadIdx.x;
+  const int pr = t % nv, grp = t / nv;
+  const bool worker = grp < groups;
+  const int a = pr / k, b = pr - (pr / k) * k;
+  Acc<T> acc;
+  acc.init();
+  const int64_t ntiles = (n + kGramTile - 1) / kGramTile;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t r0 = tile * kGramTile;
+    const int rows = (int)min((int64_t)kGramTile, n - r0);
+    const int cnt = rows * k;
+    __syncthreads();  // the previous tile has been consumed
+    {  // tiles start at multiples of kGramTile rows: 16-byte aligned
+      using V = Vec16<T>;
+      using VT = typename V::type;
+      const int cv = cnt / V::W;
+      const VT* ga = reinterpret_cast<const VT*>(A + r0 * k);
+      const VT* gb = reinterpret_cast<const VT*>(B + r0 * k);
+      for (int e = t; e < cv; e += kSolveBlock) {
+        reinterpret_cast<VT*>(sa)[e] = ga[e];
+        reinterpret_cast<VT*>(sb)[e] = gb[e];
+      }
+      for (int e = cv * V::W + t; e < cnt; e += kSolveBlock) {
+        sa[e] = A[r0 * k + e];
+        sb[e] = B[r0 * k + e];
       }
     }
+    __syncthreads();
+    if (worker) {  // the tile's share in plain FMAs, then one compensated add
+      T part = T(0);
+      for (int r = grp; r < rows; r += groups) part = fma(sa[r * k + a], sb[r * k + b], part);
+      acc.add(part);
+    }
   }
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int pr = lane + 32 * q;
-    if (q < npl && pr < nv) s_w[w][pr] = acc[q].get();
-  }
+  s_part[t] = worker ? acc.get() : red_zero(R());
   __syncthreads();
-  for (int t = threadIdx.x; t < nv; t += kSolveBlock) {
-    R s = red_zero(R());
-    for (int ww = 0; ww < kSolveBlock / 32; ++ww) s = red_add(s, s_w[ww][t]);
-    s_blk[t] = s;
+  if (t < nv) {
+    R sum = red_zero(R());
+    for (int q = 0; q < groups; ++q) sum = red_add(sum, s_part[q * nv + t]);
+    s_blk[t] = sum;
   }
   __syncthreads();
   if (!grid_reduce_rt<R>(s_blk, s_tot, nv, gr)) return;
-  for (int t = threadIdx.x; t < nv; t += kSolveBlock) G[t] = red_to_double(s_tot[t]);
+  for (int q = threadIdx.x; q < nv; q += kSolveBlock) G[q] = red_to_double(s_tot[q]);
+}
+
+// k rounded up to the register-array width the row kernels are built for
+__host__ __device__ constexpr int k_bucket(int k) { return k <= 4 ? 4 : k <= 8 ? 8 : 16; }
+
+// a k x k FP64 matrix as T in shared memory with row stride KM, zero padded
+template <typename T, int KM>
+__device__ __forceinline__ void stage_matrix(T* dst, const double* M, int k) {
+  for (int t = threadIdx.x; t < KM * KM; t += blockDim.x) {
+    const int a = t / KM, b = t - (t / KM) * KM;
+    dst[t] = (M && a < k && b < k) ? (T)M[a * k + b] : T(0);
+  }
+}
+
+// row i of an n x k block into registers (zero padded to KM); 16-byte loads
+// when k fills the bucket (rows are then 16-byte aligned)
+template <typename T, int KM>
+__device__ __forceinline__ void load_krow(const T* __restrict__ src, int64_t i, int k, T (&v)[KM]) {
+  using V = Vec16<T>;
+  using VT = typename V::type;
+  if (k == KM) {
+    const VT* p = reinterpret_cast<const VT*>(src + i * KM);
+#pragma unroll
+    for (int c = 0; c < KM / V::W; ++c) {
+      const VT x = p[c];
+#pragma unroll
+      for (int w = 0; w < V::W; ++w) v[c * V::W + w] = V::get(x, w);
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < KM; ++a) v[a] = a < k ? src[i * k + a] : T(0);
+  }
+}
+
+template <typename T, int KM>
+__device__ __forceinline__ void store_krow(T* dst, int64_t i, int k, const T (&v)[KM]) {
+  using V = Vec16<T>;
+  using VT = typename V::type;
+  if (k == KM) {
+    VT* p = reinterpret_cast<VT*>(dst + i * KM);
+#pragma unroll
+    for (int c = 0; c < KM / V::W; ++c) {
+      VT x;
+#pragma unroll
+      for (int w = 0; w < V::W; ++w) V::set(x, w, v[c * V::W + w]);
+      p[c] = x;
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < KM; ++a)
+      if (a < k) dst[i * k + a] = v[a];
+  }
 }
 
 // --------------------------------------------------------------- dots ---
@@ -195,11 +287,26 @@ __global__ void __launch_bounds__(kSolveBlock) dots_kernel(DotPairs<T> dp, int64
   using R = typename RedT<T>::type;
   if (done && *done) return;
   __shared__ R s_blk[4], s_tot[4];
+  using V = Vec16<T>;
+  using VT = typename V::type;
+  constexpr int W = V::W;
   Acc<T> acc[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) acc[q].init();
-  for (int64_t e = blockIdx.x * (int64_t)kSolveBlock + threadIdx.x; e < m;
-       e += (int64_t)gridDim.x * kSolveBlock) {
+  const int64_t mv = m / W;
+  const int64_t tid = blockIdx.x * (int64_t)kSolveBlock + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * kSolveBlock;
+  for (int64_t e = tid; e < mv; e += nth) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (q < dp.np) {
+        const VT x = reinterpret_cast<const VT*>(dp.x[q])[e];
+        const VT y = reinterpret_cast<const VT*>(dp.y[q])[e];
+#pragma unroll
+        for (int w = 0; w < W; ++w) acc[q].add(V::get(x, w) * V::get(y, w));
+      }
+  }
+  for (int64_t e = mv * W + tid; e < m; e += nth) {
 #pragma unroll
     for (int q = 0; q < 4; ++q)
       if (q < dp.np) acc[q].add(dp.x[q][e] * dp.y[q][e]);
@@ -214,67 +321,88 @@ __global__ void __launch_bounds__(kSolveBlock) dots_kernel(DotPairs<T> dp, int64
 
 // ---------------------------------------------------------- row combine ---
 // out_i = alpha X_i + beta Y_i - (P_i M1) - (Q_i M2)  for rows i, with M1,
-// M2 k x k FP64 (either may be NULL) and scalar alpha/beta.
-template <typename T>
+// M2 k x k FP64 (either may be NULL) and scalar alpha/beta.  A thread per row.
+template <typename T, int KM>
 __global__ void __launch_bounds__(kSolveBlock) combine_kernel(
     T* out, const T* X, double alpha, const T* Y, double beta, const T* P, const double* M1,
     const T* Qm, const double* M2, int64_t n, int k, const int* done) {
   if (done && *done) return;
-  __shared__ T m1[kMaxK * kMaxK], m2[kMaxK * kMaxK];
-  for (int t = threadIdx.x; t < k * k; t += kSolveBlock) {
-    m1[t] = M1 ? (T)M1[t] : T(0);
-    m2[t] = M2 ? (T)M2[t] : T(0);
-  }
+  __shared__ T m1[KM * KM], m2[KM * KM];
+  stage_matrix<T, KM>(m1, M1, k);
+  stage_matrix<T, KM>(m2, M2, k);
   __syncthreads();
-  const int64_t m = n * k;
-  for (int64_t e = blockIdx.x * (int64_t)kSolveBlock + threadIdx.x; e < m;
-       e += (int64_t)gridDim.x * kSolveBlock) {
-    const int64_t i = e / k;
-    const int b = (int)(e - i * k);
-    T v = X ? (T)alpha * X[e] : T(0);
-    if (Y) v += (T)beta * Y[e];
-    if (M1) {
-      const T* pr = P + i * k;
-      for (int a = 0; a < k; ++a) v -= pr[a] * m1[a * k + b];
+  // read through volatile views: one shared-memory load per use, so the
+  // k x k matrices are not hoisted into registers across rows
+  const volatile T* v1 = m1;
+  const volatile T* v2 = m2;
+  for (int64_t i = blockIdx.x * (int64_t)kSolveBlock + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kSolveBlock) {
+    T v[KM], xr[KM], pr[KM];
+    if (X) {
+      load_krow<T, KM>(X, i, k, xr);
+#pragma unroll
+      for (int b = 0; b < KM; ++b) v[b] = (T)alpha * xr[b];
+    } else {
+#pragma unroll
+      for (int b = 0; b < KM; ++b) v[b] = T(0);
+    }
+    if (Y) {
+      load_krow<T, KM>(Y, i, k, xr);
+#pragma unroll
+      for (int b = 0; b < KM; ++b) v[b] += (T)beta * xr[b];
+    }
+    if (M1) {  // padded rows/columns of the staged matrix are zero
+      load_krow<T, KM>(P, i, k, pr);
+#pragma unroll
+      for (int a = 0; a < KM; ++a)
+#pragma unroll
+        for (int b = 0; b < KM; ++b) v[b] -= pr[a] * v1[a * KM + b];
     }
     if (M2) {
-      const T* qr = Qm + i * k;
-      for (int a = 0; a < k; ++a) v -= qr[a] * m2[a * k + b];
+      load_krow<T, KM>(Qm, i, k, pr);
+#pragma unroll
+      for (int a = 0; a < KM; ++a)
+#pragma unroll
+        for (int b = 0; b < KM; ++b) v[b] -= pr[a] * v2[a * KM + b];
     }
-    out[e] = v;
+    store_krow<T, KM>(out, i, k, v);
   }
 }
 
 // ------------------------------------------------------ Riemannian Hessian ---
 // Hd = He - U G - delta M   and the partial sum of <delta, Hd>; the last
 // block takes truncated CG's curvature step (alpha, or the boundary tau).
-template <typename T>
+// A thread per row.
+template <typename T, int KM>
 __global__ void __launch_bounds__(kSolveBlock) hess_kernel(T* Hd, const T* He, const T* U,
                                                            const double* G, const T* delta,
                                                            const double* M, int64_t n, int k,
                                                            TcgState* st, GridRed gr) {
   using R = typename RedT<T>::type;
   if (st->done) return;
-  __shared__ T g[kMaxK * kMaxK], mm[kMaxK * kMaxK];
+  __shared__ T g[KM * KM], mm[KM * KM];
   __shared__ R s_blk[1], s_tot[1];
-  for (int t = threadIdx.x; t < k * k; t += kSolveBlock) {
-    g[t] = (T)G[t];
-    mm[t] = (T)M[t];
-  }
+  stage_matrix<T, KM>(g, G, k);
+  stage_matrix<T, KM>(mm, M, k);
   __syncthreads();
+  const volatile T* gv = g;  // one shared-memory load per use (see combine_kernel)
+  const volatile T* mv = mm;
   Acc<T> acc;
   acc.init();
-  const int64_t m = n * k;
-  for (int64_t e = blockIdx.x * (int64_t)kSolveBlock + threadIdx.x; e < m;
-       e += (int64_t)gridDim.x * kSolveBlock) {
-    const int64_t i = e / k;
-    const int b = (int)(e - i * k);
-    T v = He[e];
-    const T* ur = U + i * k;
-    const T* dr = delta + i * k;
-    for (int a = 0; a < k; ++a) v -= ur[a] * g[a * k + b] + dr[a] * mm[a * k + b];
-    Hd[e] = v;
-    acc.add(delta[e] * v);
+  for (int64_t i = blockIdx.x * (int64_t)kSolveBlock + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kSolveBlock) {
+    T v[KM], ur[KM], dr[KM];
+    load_krow<T, KM>(He, i, k, v);
+    load_krow<T, KM>(U, i, k, ur);
+    load_krow<T, KM>(delta, i, k, dr);
+#pragma unroll
+    for (int a = 0; a < KM; ++a)
+#pragma unroll
+      for (int b = 0; b < KM; ++b) v[b] -= ur[a] * gv[a * KM + b] + dr[a] * mv[a * KM + b];
+    store_krow<T, KM>(Hd, i, k, v);
+#pragma unroll
+    for (int b = 0; b < KM; ++b)
+      if (b < k) acc.add(dr[b] * v[b]);
   }
   R v1[1] = {acc.get()};
   block_sum<R, 1>(v1, s_blk);
@@ -312,10 +440,38 @@ __global__ void __launch_bounds__(kSolveBlock) cg_update_kernel(T* eta, T* Heta,
   const T step = (T)st->step;
   const T alpha = (T)st->alpha;
   const bool bnd = st->boundary != 0;
+  using V = Vec16<T>;
+  using VT = typename V::type;
+  constexpr int W = V::W;
   Acc<T> acc;
   acc.init();
-  for (int64_t e = blockIdx.x * (int64_t)kSolveBlock + threadIdx.x; e < m;
-       e += (int64_t)gridDim.x * kSolveBlock) {
+  const int64_t mv = m / W;
+  const int64_t tid = blockIdx.x * (int64_t)kSolveBlock + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * kSolveBlock;
+  for (int64_t e = tid; e < mv; e += nth) {
+    const VT h = reinterpret_cast<const VT*>(Hd)[e];
+    const VT d = reinterpret_cast<const VT*>(delta)[e];
+    VT et = reinterpret_cast<VT*>(eta)[e];
+    VT he = reinterpret_cast<VT*>(Heta)[e];
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      V::set(et, w, V::get(et, w) + step * V::get(d, w));
+      V::set(he, w, V::get(he, w) + step * V::get(h, w));
+    }
+    reinterpret_cast<VT*>(eta)[e] = et;
+    reinterpret_cast<VT*>(Heta)[e] = he;
+    if (!bnd) {
+      VT rr = reinterpret_cast<VT*>(r)[e];
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        const T rn = V::get(rr, w) + alpha * V::get(h, w);
+        V::set(rr, w, rn);
+        acc.add(rn * rn);
+      }
+      reinterpret_cast<VT*>(r)[e] = rr;
+    }
+  }
+  for (int64_t e = mv * W + tid; e < m; e += nth) {
     const T h = Hd[e];
     eta[e] += step * delta[e];
     Heta[e] += step * h;
@@ -360,9 +516,20 @@ __global__ void __launch_bounds__(kSolveBlock) direction_kernel(T* delta, const 
                                                                 const TcgState* st) {
   if (st->done) return;
   const T beta = (T)st->beta;
-  for (int64_t e = blockIdx.x * (int64_t)kSolveBlock + threadIdx.x; e < m;
-       e += (int64_t)gridDim.x * kSolveBlock)
-    delta[e] = -r[e] + beta * delta[e];
+  using V = Vec16<T>;
+  using VT = typename V::type;
+  constexpr int W = V::W;
+  const int64_t mv = m / W;
+  const int64_t tid = blockIdx.x * (int64_t)kSolveBlock + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * kSolveBlock;
+  for (int64_t e = tid; e < mv; e += nth) {
+    const VT rr = reinterpret_cast<const VT*>(r)[e];
+    VT d = reinterpret_cast<VT*>(delta)[e];
+#pragma unroll
+    for (int w = 0; w < W; ++w) V::set(d, w, -V::get(rr, w) + beta * V::get(d, w));
+    reinterpret_cast<VT*>(delta)[e] = d;
+  }
+  for (int64_t e = mv * W + tid; e < m; e += nth) delta[e] = -r[e] + beta * delta[e];
 }
 
 // --------------------------------------------------------- Cholesky-QR ---
@@ -399,22 +566,25 @@ __global__ void chol_inv_kernel(const double* G, int k, double* Rinv, int* bad) 
   }
 }
 
-// out_i = A_i Rinv  (rows times an upper-triangular k x k)
-template <typename T>
+// out_i = A_i Rinv  (rows times an upper-triangular k x k); a thread per row
+template <typename T, int KM>
 __global__ void __launch_bounds__(kSolveBlock) rmul_kernel(T* out, const T* A, const double* Rinv,
                                                            int64_t n, int k) {
-  __shared__ T ri[kMaxK * kMaxK];
-  for (int t = threadIdx.x; t < k * k; t += kSolveBlock) ri[t] = (T)Rinv[t];
+  __shared__ T ri[KM * KM];
+  stage_matrix<T, KM>(ri, Rinv, k);
   __syncthreads();
-  const int64_t m = n * k;
-  for (int64_t e = blockIdx.x * (int64_t)kSolveBlock + threadIdx.x; e < m;
-       e += (int64_t)gridDim.x * kSolveBlock) {
-    const int64_t i = e / k;
-    const int b = (int)(e - i * k);
-    const T* ar = A + i * k;
-    T v = T(0);
-    for (int a = 0; a <= b; ++a) v += ar[a] * ri[a * k + b];
-    out[e] = v;
+  const volatile T* rv = ri;  // one shared-memory load per use (see combine_kernel)
+  for (int64_t i = blockIdx.x * (int64_t)kSolveBlock + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kSolveBlock) {
+    T v[KM], ar[KM];
+    load_krow<T, KM>(A, i, k, ar);
+#pragma unroll
+    for (int b = 0; b < KM; ++b) v[b] = T(0);
+#pragma unroll
+    for (int a = 0; a < KM; ++a)
+#pragma unroll
+      for (int b = a; b < KM; ++b) v[b] += ar[a] * rv[a * KM + b];  // Rinv upper triangular
+    store_krow<T, KM>(out, i, k, v);
   }
 }
 

@@ -23,6 +23,10 @@ benchmarked on:
               w ~ U[0.1,1]  (k=16)
   sbm_batch   512 SBMs with n log-uniform in [500, 50,000], 2..8 blocks,
               mean degree 8..20, unit weights, k in {2,4,8} per graph
+  delaunayR   Delaunay triangulation of 2^R points uniform in the unit
+              square, unit weights (about 6n stored entries), R = 16..19:
+              the construction of the paper's Delaunay matrices, drawn
+              afresh  (k=4)
 
 Every graph is undirected: both triangles are stored, rows hold sorted column
 indices, there are no self loops and no duplicate entries.
@@ -296,6 +300,19 @@ def sbm_batch(seed: int, n_graphs: int = 512, n_lo: int = 500, n_hi: int = 50_00
     return concat_graphs(graphs, ks)
 
 
+def delaunay_unit_square(seed: int, n: int, val_dtype=np.float32) -> CSRGraph:
+    """Delaunay triangulation of n points drawn uniformly in [0,1]^2 (scipy's
+    Qhull), every triangle side an undirected edge of weight 1."""
+    from scipy.spatial import Delaunay
+    rng = np.random.default_rng(seed)
+    pts = rng.random((n, 2))
+    tri = Delaunay(pts).simplices.astype(np.int64)
+    e = np.concatenate([tri[:, [0, 1]], tri[:, [1, 2]], tri[:, [0, 2]]])
+    e.sort(axis=1)
+    e = np.unique(e, axis=0)
+    return csr_from_undirected(n, e[:, 0], e[:, 1], np.ones(len(e)), val_dtype)
+
+
 # --------------------------------------------------------------------------
 # dense blocks
 # --------------------------------------------------------------------------
@@ -327,6 +344,9 @@ WORKLOADS = {
     "dcsbm": dict(index=3, k=16, p_schedule=(1.3,)),
     "sbm_batch": dict(index=4, k=None, p_schedule=tuple(round(2.0 - 0.1 * i, 1) for i in range(9))),
 }
+for _r in (16, 17, 18, 19):
+    WORKLOADS[f"delaunay{_r}"] = dict(index=5 + _r - 16, k=4,
+                                      p_schedule=tuple(round(2.0 - 0.1 * i, 1) for i in range(10)))
 
 
 def make_graph(name: str, val_dtype=np.float32):
@@ -343,6 +363,8 @@ def make_graph(name: str, val_dtype=np.float32):
         return dcsbm_powerlaw(seed, val_dtype=val_dtype)
     if name == "sbm_batch":
         return sbm_batch(seed, val_dtype=val_dtype)
+    if name.startswith("delaunay"):
+        return delaunay_unit_square(seed, 1 << int(name[len("delaunay"):]), val_dtype=val_dtype)
     raise KeyError(name)
 
 

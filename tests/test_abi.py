@@ -103,3 +103,33 @@ def test_calls_reject_null_graph_and_bad_arguments(lib):
     out = C.c_double()
     assert lib.pspec_rcut(None, None, 2, C.byref(out), None) == _abi.PSPEC_ERR_INVALID_ARG
     lib.pspec_graph_destroy(None)  # accepted
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of the option, statistics and tuning structs have the
+    C layout of include/pspec.h: sizes and every field offset, printed by a C
+    program compiled against the header."""
+    import shutil
+    import subprocess
+    from paper_2605_26975_gb300 import _abi
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"pspec_solve_opts": _abi.SolveOpts, "pspec_solve_stats": _abi.SolveStats,
+               "pspec_tune_report": _abi.TuneReport}
+    lines = ['#include <stdio.h>', '#include "pspec.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == C.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
