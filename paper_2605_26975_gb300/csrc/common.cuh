@@ -44,16 +44,6 @@ __device__ __forceinline__ float abs_pow_pm2_clamped(float x, float pm2) {
   return ex2_approx(pm2 * t);
 }
 
-// Fire-and-forget bulk prefetch of [p, p + bytes) into L2 (TMA unit; no
-// shared memory, no barrier).  The window is widened to 16-byte boundaries,
-// so the caller's allocation must extend 16 bytes past the last byte asked.
-__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
-  const uintptr_t a = (uintptr_t)p & ~(uintptr_t)15;
-  const uintptr_t e = ((uintptr_t)p + bytes + 15) & ~(uintptr_t)15;
-  if (e > a)
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(e - a)) : "memory");
-}
-
 // ------------------------------------------------- TMA bulk copy + mbarrier ---
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -103,22 +93,6 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t
           smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
-}
-
-// ------------------------------------------------- per-thread async copies ---
-// cp.async global -> shared of 4, 8 or 16 bytes (both addresses aligned to the
-// size); completion is tracked per thread in commit groups.
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void* dst, const void* src) {
-  static_assert(BYTES == 4 || BYTES == 8 || BYTES == 16, "cp.async size");
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-// wait until at most N of this thread's most recent groups are pending
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // ---------------------------------------------------------------- Kahan ---

@@ -39,7 +39,7 @@ struct SolveWork {
   TcgState* st;
   int* bad;
   GridRed gr;
-  int vblocks, gblocks, rblocks;  // elementwise, Gram, row kernels
+  int vblocks, gblocks, rblocks, tblocks;  // elementwise, Gram, row kernels, TMA Gram
 };
 
 template <typename T>
@@ -51,6 +51,8 @@ pspec_status carve(pspec_graph* g, int k, SolveWork<T>* w) {
                                                            (g->n + kGramTile - 1) / kGramTile));
   w->rblocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * 4,
                                                            (g->n + kSolveBlock - 1) / kSolveBlock));
+  w->tblocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * 3,
+                                                           (g->n + kGramTile - 1) / kGramTile));
   const int maxb = std::max(w->vblocks, w->gblocks);
   const int groups = (maxb + kGroup - 1) / kGroup;
   const size_t red = sizeof(double) * 256 * (size_t)(maxb + groups);
@@ -150,7 +152,23 @@ struct Solver {
   }
   pspec_status gram(const T* A, const T* B, double* G, const int* done = nullptr) {
     TimedScope timer(g, "solve_gram", s);
-    gram_kernel<T><<<w.gblocks, kSolveBlock, 0, s>>>(A, B, n, k, G, w.gr, done);
+    if constexpr (sizeof(T) == 4) {
+      if (k % 4 != 0) {
+        gram_kernel<T><<<w.gblocks, kSolveBlock, 0, s>>>(A, B, n, k, G, w.gr, done);
+        PSPEC_CUDA(cudaGetLastError());
+        return PSPEC_OK;
+      }
+      static bool attr = false;
+      if (!attr) {
+        PSPEC_CUDA(cudaFuncSetAttribute(gram_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)gram_tma_smem_bytes()));
+        attr = true;
+      }
+      gram_tma_kernel<<<w.tblocks, kSolveBlock, gram_tma_smem_bytes(), s>>>(A, B, n, k, G, w.gr, done,
+                                                                             g->d_status);
+    } else {
+      gram_kernel<T><<<w.gblocks, kSolveBlock, 0, s>>>(A, B, n, k, G, w.gr, done);
+    }
     PSPEC_CUDA(cudaGetLastError());
     return PSPEC_OK;
   }

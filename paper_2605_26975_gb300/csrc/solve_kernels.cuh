@@ -220,6 +220,163 @@ __global__ void __launch_bounds__(kSolveBlock) gram_kernel(const T* __restrict__
   for (int q = threadIdx.x; q < nv; q += kSolveBlock) G[q] = red_to_double(s_tot[q]);
 }
 
+// The FP32 Gram product for k a multiple of 4, with the tiles streamed by the
+// TMA unit: a ring of kGramStages stages per block, each holding one full
+// tile of A and of B, filled by two 1-D bulk copies (one elected thread) that
+// complete on the stage's mbarrier; a stage is refilled with the block's tile
+// kGramStages ahead as soon as all threads have read it.  Full tiles are 128
+// rows of k floats (512k bytes, 16-byte aligned in the 256-byte aligned
+// solver buffers); a ragged last tile is read with plain loads.  A thread
+// owns a 4 x 4 block of the k x k output and a share of every tile's rows: a
+// row costs it two 16-byte shared loads and 16 FMAs (each staged value is
+// read k/4 times, not k).  Per-thread sums are FP32 within four tiles, then
+// compensated.  Every wait is bounded: a block that gives up records a
+// timeout in *status, waits (bounded) for its copies still in flight and
+// leaves the sums undone.
+constexpr int kGramStages = 3;
+constexpr uint32_t kGramWaitTries = 2000;  // x up to 1 ms each
+constexpr size_t kGramTileFloats = (size_t)kGramTile * kMaxK;
+constexpr size_t gram_tma_smem_bytes() {
+  return sizeof(float) * 2 * kGramTileFloats * kGramStages + sizeof(uint64_t) * kGramStages;
+}
+
+__global__ void __launch_bounds__(kSolveBlock) gram_tma_kernel(const float* __restrict__ A,
+                                                               const float* __restrict__ B,
+                                                               int64_t n, int k, double* G,
+                                                               GridRed gr, const int* done,
+                                                               int* status) {
+  using R = float2;
+  if (done && *done) return;
+  extern __shared__ __align__(128) unsigned char gsm[];
+  float* tiles = reinterpret_cast<float*>(gsm);  // [stage][A|B][kGramTileFloats]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(gsm + sizeof(float) * 2 * kGramTileFloats * kGramStages);
+  __shared__ R s_blk[kMaxK * kMaxK];
+  __shared__ R s_tot[kMaxK * kMaxK];
+  const int nv = k * k;
+  const int nb = k / 4;                  // 4 x 4 output blocks per side
+  const int nblk = nb * nb;
+  const int groups = kSolveBlock / nblk;  // row groups
+  const int t = threadIdx.x;
+  const int pb = t % nblk, grp = t / nblk;
+  const bool worker = grp < groups;
+  const int a0 = 4 * (pb / nb), b0 = 4 * (pb % nb);
+  const int64_t nfull = n / kGramTile;
+  const uint32_t tbytes = (uint32_t)(kGramTile * k * sizeof(float));
+  auto issue = [&](int stage, int64_t tile) {
+    float* dst = tiles + (size_t)stage * 2 * kGramTileFloats;
+    mbar_arrive_expect_tx(&bars[stage], 2u * tbytes);
+    tma_load_1d(dst, A + tile * kGramTile * k, tbytes, &bars[stage]);
+    tma_load_1d(dst + kGramTileFloats, B + tile * kGramTile * k, tbytes, &bars[stage]);
+  };
+  if (t == 0) {
+    for (int st = 0; st < kGramStages; ++st) mbar_init(&bars[st], 1);
+    mbar_init_fence();
+    for (int st = 0; st < kGramStages; ++st) {
+      const int64_t tile = blockIdx.x + (int64_t)st * gridDim.x;
+      if (tile < nfull) issue(st, tile);
+    }
+  }
+  __syncthreads();
+  Kahan acc[16];
+  float part[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    acc[q].init();
+    part[q] = 0.f;
+  }
+  // rows [r_lo, r_hi) of a staged tile into the 4 x 4 block
+  auto accumulate = [&](const float* sa, const float* sb, int rows) {
+    for (int r = grp; r < rows; r += groups) {
+      const float4 av = *reinterpret_cast<const float4*>(sa + r * k + a0);
+      const float4 bv = *reinterpret_cast<const float4*>(sb + r * k + b0);
+      const float aa[4] = {av.x, av.y, av.z, av.w};
+      const float bb[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) part[i * 4 + j] = fmaf(aa[i], bb[j], part[i * 4 + j]);
+    }
+  };
+  auto flush = [&]() {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      acc[q].add(part[q]);
+      part[q] = 0.f;
+    }
+  };
+  uint32_t phase = 0;
+  int it = 0;
+  bool timed_out = false;
+  for (int64_t tile = blockIdx.x; tile < nfull; tile += gridDim.x, ++it) {
+    const int st = it % kGramStages;
+    const bool got = mbar_wait_bounded(&bars[st], (phase >> st) & 1u, kGramWaitTries);
+    if (!__syncthreads_and(got)) {
+      timed_out = true;
+      break;
+    }
+    phase ^= 1u << st;
+    const float* sa = tiles + (size_t)st * 2 * kGramTileFloats;
+    const float* sb = sa + kGramTileFloats;
+    if (worker) {
+      accumulate(sa, sb, kGramTile);
+      if ((it & 3) == 3) flush();
+    }
+    __syncthreads();  // every thread has read the stage: refill it
+    if (t == 0) {
+      const int64_t next = tile + (int64_t)kGramStages * gridDim.x;
+      if (next < nfull) {
+        fence_proxy_async_smem();
+        issue(st, next);
+      }
+    }
+  }
+  if (timed_out) {
+    if (t == 0) {
+      atomicOr(status, kStatusTimeout);
+      // wait (bounded) for this block's copies still in flight
+      int64_t tile = blockIdx.x + (int64_t)it * gridDim.x;
+      for (int q = 0; q < kGramStages && tile < nfull; ++q, ++it, tile += gridDim.x) {
+        const int st = it % kGramStages;
+        mbar_wait_bounded(&bars[st], (phase >> st) & 1u, kGramWaitTries);
+        phase ^= 1u << st;
+      }
+    }
+    __syncthreads();
+    return;
+  }
+  // the ragged last tile, read with plain loads by the block whose turn it is
+  const int rows = (int)(n - nfull * kGramTile);
+  if (rows > 0 && blockIdx.x == (int)(nfull % gridDim.x)) {
+    float* sa = tiles;  // every copy of this block has landed and been read
+    float* sb = tiles + kGramTileFloats;
+    const int64_t r0 = nfull * kGramTile;
+    for (int e = t; e < rows * k; e += kSolveBlock) {
+      sa[e] = A[r0 * k + e];
+      sb[e] = B[r0 * k + e];
+    }
+    __syncthreads();
+    if (worker) accumulate(sa, sb, rows);
+  }
+  if (worker) flush();
+  // the row groups of each output entry in order (the stages are free now:
+  // every copy of this block has landed and been read)
+  __syncthreads();
+  float2* s_part = reinterpret_cast<float2*>(tiles);  // [16][kSolveBlock]
+#pragma unroll
+  for (int q = 0; q < 16; ++q) s_part[q * kSolveBlock + t] = worker ? kahan_to_ff(acc[q]) : make_float2(0.f, 0.f);
+  __syncthreads();
+  if (t < nv) {
+    const int a = t / k, b = t - (t / k) * k;
+    const int blk = (a / 4) * nb + (b / 4), q = (a % 4) * 4 + (b % 4);
+    R sum = make_float2(0.f, 0.f);
+    for (int g2 = 0; g2 < groups; ++g2) sum = red_add(sum, s_part[q * kSolveBlock + g2 * nblk + blk]);
+    s_blk[t] = sum;
+  }
+  __syncthreads();
+  if (!grid_reduce_rt<R>(s_blk, s_tot, nv, gr)) return;
+  for (int q = threadIdx.x; q < nv; q += kSolveBlock) G[q] = red_to_double(s_tot[q]);
+}
+
 // k rounded up to the register-array width the row kernels are built for
 __host__ __device__ constexpr int k_bucket(int k) { return k <= 4 ? 4 : k <= 8 ? 8 : 16; }
 

@@ -139,3 +139,19 @@ def test_solve_rejects_bad_schedule(api):
     for sched in ([1.5, 1.8], [2.2], [1.0]):
         with pytest.raises(_abi.PspecError):
             G.solve(U0, sched)
+
+
+def test_graph_replayed_solve_equals_eager_solve(api):
+    """The solve replays chunks of tCG iterations as CUDA graphs; with kernel
+    timing on it launches every kernel eagerly.  Both run the same kernels in
+    the same order, so the results are bit-identical."""
+    g = wl.make_graph("sbm4")
+    sched = (2.0, 1.6)
+    U0 = torch.from_numpy(wl.orthonormal_block(2000, g.n, 4, np.float32)).cuda()
+    G = api.Graph.from_csr(g)
+    U1, lab1, rc1, st1, _ = G.solve(U0, sched, api.default_opts())
+    G.set_timing(True)
+    U2, lab2, rc2, st2, _ = G.solve(U0, sched, api.default_opts())
+    G.set_timing(False)
+    assert torch.equal(U1, U2) and torch.equal(lab1, lab2)
+    assert rc1 == rc2 and st1["hvp_calls"] == st2["hvp_calls"]
