@@ -254,6 +254,30 @@ pspec_status pspec_solve(pspec_graph* g, int k, const double* p_schedule, int n_
                          int32_t* labels_out, double* rcut_out, pspec_solve_stats* stats,
                          void* stream);
 
+/* ------------------------------------------------------ solve, batched ---
+ * pspec_solve_batched: pspec_solve for every graph of a batched handle, each
+ * graph its own problem (its own trust regions, truncated CG, k-means and
+ * RCut), with the same k for all graphs.  The first call builds one
+ * single-graph handle per graph (kept on the batched handle, freed with it);
+ * the per-graph solves then run concurrently, n_threads host threads taking
+ * graphs in turn, each solve on its graph handle's private stream.  Every
+ * graph's result equals pspec_solve on that graph alone.
+ *   U_inout     device n x k FP32 (the concatenation): each graph's U0 in,
+ *               final U out
+ *   labels_out  device int32[n]: each graph's k-means labels, 0..k-1
+ *   rcut_out    host double[G]: each graph's RCut (NaN where the graph has
+ *               fewer vertices than k, 0 for an empty graph)
+ *   status_out  host int32[G]: each graph's pspec_status
+ * Synchronises `stream` before and after.  Returns OK, NOT_CONVERGED when a
+ * graph's stage hit max_outer, or the first graph error (INVALID_ARG when a
+ * graph has fewer vertices than k, CUDA, OOM, NONFINITE), with its graph
+ * named in pspec_last_error.  The paper solves one graph; batching is this
+ * library's. */
+pspec_status pspec_solve_batched(pspec_graph* g, int k, const double* p_schedule, int n_p,
+                                 const pspec_solve_opts* opts, float* U_inout, int32_t* labels_out,
+                                 double* rcut_out, int32_t* status_out, int n_threads, void* stream);
+
+
 /* --------------------------------------------------------------- kmeans ---
  * pspec_kmeans: k-means of the n rows of X (n x dim, row-major, dtype,
  * device), the discretisation step of Section 1/2.  k-means++ seeding whose

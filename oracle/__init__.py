@@ -14,8 +14,10 @@ taken.  The pins that tie each function to something other than itself live in
 
 Parity status: every function is pinned except the p < 2 stages of the solve,
 which the method reaches by a heuristic continuation with no closed form
-("parity unpinned" for ``manifold.solve`` below p = 2; it is checked only by
-agreement of the two implementations and by its p = 2 stage).
+("parity unpinned" for ``manifold.solve`` below p = 2, with either Hessian
+form; it is checked only by agreement of the two implementations and by its
+p = 2 stage, where the exact and Algorithm 1 forms give the same projected
+Hessian).
 """
 from .plap import (edge_list, phi_p, abs_pow_pm2, p_norm_p, objective_parts, objective,
                    p_laplacian, euclidean_grad, euclidean_hvp, alg1_sparse_hvp)

@@ -169,6 +169,28 @@ class Graph:
                   kmeans_inertia=stats.kmeans_inertia)
         return U, lab, rc.value, sd, st
 
+    def solve_batched(self, U0, p_schedule, opts=None, threads=16):
+        """pspec_solve_batched on a batched handle: every graph solved on its
+        own, concurrently.  U0 is the concatenated n x k FP32 block.  Returns
+        (U, labels (per-graph 0..k-1), rcut per graph, status per graph,
+        overall status)."""
+        if self.n_graphs < 1:
+            raise ValueError("not a graph handle")
+        U = _dev_block(U0, "U0", self.n).clone()
+        if U.dtype != torch.float32:
+            raise TypeError("the batched solve runs the FP32 path")
+        k = U.shape[1]
+        o = default_opts() if opts is None else opts
+        sched = np.ascontiguousarray(p_schedule, dtype=np.float64)
+        lab = torch.empty(self.n, dtype=torch.int32, device=U.device)
+        rc = np.zeros(self.n_graphs, dtype=np.float64)
+        status = np.zeros(self.n_graphs, dtype=np.int32)
+        st = lib().pspec_solve_batched(self._h, k, sched.ctypes.data, sched.size, C.byref(o), _ptr(U),
+                                       _ptr(lab), rc.ctypes.data, status.ctypes.data, int(threads),
+                                       _stream())
+        check(st, "pspec_solve_batched", allow=(_abi.PSPEC_OK, _abi.PSPEC_ERR_NOT_CONVERGED))
+        return U, lab, rc, status, st
+
     def rcut(self, labels, n_clusters):
         if not labels.is_cuda or labels.dtype != torch.int32:
             raise TypeError("labels must be an int32 CUDA tensor")

@@ -470,6 +470,8 @@ pspec_status pspec_graph_create_batched(int32_t n_graphs, const int64_t* node_of
 
 void pspec_graph_destroy(pspec_graph* g) {
   if (!g) return;
+  for (pspec_graph* sub : g->subs) pspec_graph_destroy(sub);
+  g->subs.clear();
   for (auto& ts : g->tasks) {
     free_tasks(ts);
   }

@@ -108,6 +108,9 @@ struct pspec_graph {
   // stream is (capture is not possible on the legacy default stream)
   cudaStream_t solve_stream = nullptr;
   cudaEvent_t solve_event = nullptr;
+  // batches: one single-graph handle per graph, built by the first
+  // pspec_solve_batched call (columns rebased to the graph's own vertices)
+  std::vector<pspec_graph*> subs;
   pspec::Timing timing;
 };
 
@@ -189,6 +192,12 @@ pspec_status eval_batched(pspec_graph* g, const float* U, int k, double p, doubl
 pspec_status hvp_batched(pspec_graph* g, const float* U, const float* V, int k, double p,
                          float* HV, cudaStream_t s, bool alg1 = false);
 int64_t task_count(pspec_graph* g, int k);
+pspec_status check_solve_args(const double* p_schedule, int n_p, const pspec_solve_opts* opts,
+                              pspec_solve_opts* o);
+pspec_status solve_on_handle(pspec_graph* g, int k, const double* p_schedule, int n_p,
+                             const pspec_solve_opts& o, pspec_dtype dtype, void* U_inout,
+                             int32_t* labels_out, double* rcut_out, pspec_solve_stats* stats,
+                             cudaStream_t caller);
 
 // scalar slots in d_scalars
 constexpr int kSlotN = 0;      // [16]

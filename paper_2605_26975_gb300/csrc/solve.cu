@@ -405,6 +405,49 @@ static pspec_status solve_impl(pspec_graph* g, int k, const double* sched, int n
   return all_converged ? PSPEC_OK : set_error(PSPEC_ERR_NOT_CONVERGED, "a stage reached max_outer");
 }
 
+// Validation shared by the solve entry points; *o gets the options (defaults
+// where opts is NULL).
+pspec_status check_solve_args(const double* p_schedule, int n_p, const pspec_solve_opts* opts,
+                              pspec_solve_opts* o) {
+  if (!p_schedule || n_p < 1) return set_error(PSPEC_ERR_INVALID_ARG, "empty p schedule");
+  for (int i = 0; i < n_p; ++i) {
+    if (!(p_schedule[i] > 1.0 && p_schedule[i] <= 2.0))
+      return set_error(PSPEC_ERR_INVALID_ARG, "every p must be in (1, 2]");
+    if (i > 0 && p_schedule[i] > p_schedule[i - 1])
+      return set_error(PSPEC_ERR_INVALID_ARG, "the p schedule must be non-increasing");
+  }
+  pspec_solve_opts_default(o);
+  if (opts) *o = *opts;
+  if (o->max_inner < 1 || o->max_outer < 0 || o->kmeans_restarts < 1)
+    return set_error(PSPEC_ERR_INVALID_ARG, "bad iteration caps");
+  if (o->hessian_form != PSPEC_HESSIAN_EXACT && o->hessian_form != PSPEC_HESSIAN_ALG1)
+    return set_error(PSPEC_ERR_INVALID_ARG, "hessian_form must be PSPEC_HESSIAN_EXACT or PSPEC_HESSIAN_ALG1");
+  return PSPEC_OK;
+}
+
+// The solve of one single-graph handle on its private stream, joined to
+// `caller` by events (validated arguments).
+pspec_status solve_on_handle(pspec_graph* g, int k, const double* p_schedule, int n_p,
+                             const pspec_solve_opts& o, pspec_dtype dtype, void* U_inout,
+                             int32_t* labels_out, double* rcut_out, pspec_solve_stats* stats,
+                             cudaStream_t caller) {
+  if (!g->solve_stream) {
+    PSPEC_CUDA(cudaStreamCreateWithFlags(&g->solve_stream, cudaStreamNonBlocking));
+    PSPEC_CUDA(cudaEventCreateWithFlags(&g->solve_event, cudaEventDisableTiming));
+  }
+  cudaStream_t s = g->solve_stream;
+  PSPEC_CUDA(cudaEventRecord(g->solve_event, caller));  // the caller's earlier work first
+  PSPEC_CUDA(cudaStreamWaitEvent(s, g->solve_event, 0));
+  const pspec_status st =
+      dtype == PSPEC_F32
+          ? solve_impl<float>(g, k, p_schedule, n_p, o, (float*)U_inout, labels_out, rcut_out, stats, s)
+          : solve_impl<double>(g, k, p_schedule, n_p, o, (double*)U_inout, labels_out, rcut_out, stats, s);
+  // whatever the solve left enqueued comes before the caller's later work
+  cudaEventRecord(g->solve_event, s);
+  cudaStreamWaitEvent(caller, g->solve_event, 0);
+  return st;
+}
+
 }  // namespace pspec
 
 using namespace pspec;
@@ -436,36 +479,10 @@ extern "C" pspec_status pspec_solve(pspec_graph* g, int k, const double* p_sched
   if (g->n_graphs != 1) return set_error(PSPEC_ERR_INVALID_ARG, "pspec_solve takes a single graph");
   if (k < 1 || k > kMaxK) return set_error(PSPEC_ERR_INVALID_ARG, "k must be in [1, 16]");
   if (k > g->n) return set_error(PSPEC_ERR_INVALID_ARG, "k exceeds n");
-  if (!p_schedule || n_p < 1) return set_error(PSPEC_ERR_INVALID_ARG, "empty p schedule");
-  for (int i = 0; i < n_p; ++i) {
-    if (!(p_schedule[i] > 1.0 && p_schedule[i] <= 2.0))
-      return set_error(PSPEC_ERR_INVALID_ARG, "every p must be in (1, 2]");
-    if (i > 0 && p_schedule[i] > p_schedule[i - 1])
-      return set_error(PSPEC_ERR_INVALID_ARG, "the p schedule must be non-increasing");
-  }
   pspec_solve_opts o;
-  pspec_solve_opts_default(&o);
-  if (opts) o = *opts;
-  if (o.max_inner < 1 || o.max_outer < 0 || o.kmeans_restarts < 1)
-    return set_error(PSPEC_ERR_INVALID_ARG, "bad iteration caps");
-  if (o.hessian_form != PSPEC_HESSIAN_EXACT && o.hessian_form != PSPEC_HESSIAN_ALG1)
-    return set_error(PSPEC_ERR_INVALID_ARG, "hessian_form must be PSPEC_HESSIAN_EXACT or PSPEC_HESSIAN_ALG1");
+  PSPEC_TRY(check_solve_args(p_schedule, n_p, opts, &o));
   PSPEC_TRY(check_block(U_inout, k, dtype, "U_inout"));
   if (dtype != PSPEC_F32 && dtype != PSPEC_F64) return set_error(PSPEC_ERR_INVALID_ARG, "bad dtype");
-  cudaStream_t caller = (cudaStream_t)stream;
-  if (!g->solve_stream) {
-    PSPEC_CUDA(cudaStreamCreateWithFlags(&g->solve_stream, cudaStreamNonBlocking));
-    PSPEC_CUDA(cudaEventCreateWithFlags(&g->solve_event, cudaEventDisableTiming));
-  }
-  cudaStream_t s = g->solve_stream;
-  PSPEC_CUDA(cudaEventRecord(g->solve_event, caller));  // the caller's earlier work first
-  PSPEC_CUDA(cudaStreamWaitEvent(s, g->solve_event, 0));
-  const pspec_status st =
-      dtype == PSPEC_F32
-          ? solve_impl<float>(g, k, p_schedule, n_p, o, (float*)U_inout, labels_out, rcut_out, stats, s)
-          : solve_impl<double>(g, k, p_schedule, n_p, o, (double*)U_inout, labels_out, rcut_out, stats, s);
-  // whatever the solve left enqueued comes before the caller's later work
-  cudaEventRecord(g->solve_event, s);
-  cudaStreamWaitEvent(caller, g->solve_event, 0);
-  return st;
+  return solve_on_handle(g, k, p_schedule, n_p, o, dtype, U_inout, labels_out, rcut_out, stats,
+                         (cudaStream_t)stream);
 }
