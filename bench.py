@@ -532,7 +532,11 @@ def main():
         t0 = time.perf_counter()
         rcuts, stat = [], []
         for pt in parts:
-            _, _, rc, status, _ = pt.G.solve_batched(pt.Ud, sched, api.default_opts())
+            # each graph's U0: orthonormal columns on its own rows, as the solve expects
+            U0 = np.concatenate([wl.orthonormal_block(2000 + 10 * pt.k + i, g.n, pt.k)
+                                 for i, g in enumerate(pt.graphs)])
+            _, _, rc, status, _ = pt.G.solve_batched(torch.from_numpy(U0).cuda(), sched,
+                                                     api.default_opts())
             rcuts.append(rc)
             stat.append(status)
         torch.cuda.synchronize()

@@ -217,6 +217,11 @@ pspec_status ensure_tasks(pspec_graph* g, int Q) {
       g->hub_part_elems = need;
     }
   }
+  // The uploads above are ordered on the legacy default stream and a
+  // cudaMemcpy from pageable memory (or a cudaMemset) may return before the
+  // device holds the data; the kernels that read the task set run on other,
+  // possibly non-blocking, streams.  Wait for them here.
+  PSPEC_CUDA(cudaStreamSynchronize(cudaStreamLegacy));
   ts.built = true;
   return PSPEC_OK;
 }
@@ -282,6 +287,9 @@ static pspec_status create_impl(int64_t n, const int64_t* rowptr_in, const int32
   if (host) {
     std::memcpy(rp.data(), rowptr_in, sizeof(int64_t) * (n + 1));
   } else {
+    // the caller's work on `s` (which may have produced the arrays) first:
+    // the copies below run on the legacy stream
+    PSPEC_CUDA(cudaStreamSynchronize(s));
     PSPEC_CUDA(cudaMemcpy(rp.data(), rowptr_in, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost));
   }
   if (rp[0] != 0) return set_error(PSPEC_ERR_INVALID_ARG, "rowptr[0] must be 0");

@@ -22,6 +22,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -258,7 +259,9 @@ static pspec_status solve_impl(pspec_graph* g, int k, const double* sched, int n
   PSPEC_CUDA(cudaMemsetAsync(w.bad, 0, sizeof(int), s));
   const int chunk = sizeof(T) == 4 ? 6 : 2;  // CG iterations per host check
   GraphCache graphs;
-  graphs.enabled = !g->timing.enabled;  // per-kernel timing needs eager launches
+  // per-kernel timing needs eager launches; PSPEC_SOLVE_EAGER=1 asks for them too
+  graphs.enabled = !g->timing.enabled && !(std::getenv("PSPEC_SOLVE_EAGER") &&
+                                           std::getenv("PSPEC_SOLVE_EAGER")[0] == '1');
   pspec_solve_stats st_local;
   std::memset(&st_local, 0, sizeof(st_local));
   bool all_converged = true;
