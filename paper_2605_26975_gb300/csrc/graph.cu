@@ -254,6 +254,10 @@ pspec_status take_status(pspec_graph* g, cudaStream_t s) {
   PSPEC_CUDA(cudaMemcpyAsync(&st, g->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
   PSPEC_CUDA(cudaStreamSynchronize(s));
   if (st != 0) PSPEC_CUDA(cudaMemsetAsync(g->d_status, 0, sizeof(int), s));
+  return status_error(st);
+}
+
+pspec_status status_error(int st) {
   if (st & kStatusNonFinite) return set_error(PSPEC_ERR_NONFINITE, "a NaN or Inf reached a sum");
   if (st & kStatusZeroColumn) return set_error(PSPEC_ERR_ZERO_COLUMN, "a column has zero p-norm");
   if (st & kStatusTimeout) return set_error(PSPEC_ERR_TIMEOUT, "a bounded device wait gave up");
@@ -496,6 +500,7 @@ void pspec_graph_destroy(pspec_graph* g) {
   cudaFree(g->d_scratch);
   cudaFree(g->d_hub_part);
   if (g->solve_stream) cudaStreamDestroy(g->solve_stream);
+  if (g->h_solve_rec) cudaFreeHost(g->h_solve_rec);
   if (g->solve_event) cudaEventDestroy(g->solve_event);
   cudaFree(g->d_block_part);
   cudaFree(g->d_group_part);

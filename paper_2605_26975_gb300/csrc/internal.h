@@ -108,6 +108,7 @@ struct pspec_graph {
   // stream is (capture is not possible on the legacy default stream)
   cudaStream_t solve_stream = nullptr;
   cudaEvent_t solve_event = nullptr;
+  void* h_solve_rec = nullptr;  // pinned 512 bytes: the solve's per-step host record
   // batches: one single-graph handle per graph, built by the first
   // pspec_solve_batched call (columns rebased to the graph's own vertices)
   std::vector<pspec_graph*> subs;
@@ -155,6 +156,7 @@ int grid_blocks(pspec_graph* g, int blocks_per_sm);
 pspec_status check_block(const void* ptr, int k, pspec_dtype dtype, const char* name);
 pspec_status check_common(pspec_graph* g, int k, double p);
 pspec_status take_status(pspec_graph* g, cudaStream_t s);
+pspec_status status_error(int status_word);  // the error a status word reports (OK if 0)
 
 // launchers (FP32 fast path), implemented per k in edge_*.cu
 struct EdgeLaunch {

@@ -35,8 +35,8 @@ namespace {
 
 template <typename T>
 struct SolveWork {
-  T *U, *Unew, *egrad, *egrad_new, *rg, *eta, *Heta, *r, *delta, *He, *Hd, *tmp;
-  double *M, *G, *Gram, *Rinv, *dots, *F;
+  T *U, *Unew, *egrad, *egrad_new, *rg, *rg_new, *eta, *Heta, *r, *delta, *He, *Hd, *tmp;
+  double *M, *Mnew, *G, *Gram, *Rinv, *dots, *gdot, *F;
   TcgState* st;
   int* bad;
   GridRed gr;
@@ -58,7 +58,7 @@ pspec_status carve(pspec_graph* g, int k, SolveWork<T>* w) {
   const int groups = (maxb + kGroup - 1) / kGroup;
   const size_t red = sizeof(double) * 256 * (size_t)(maxb + groups);
   const size_t small = 4096 * sizeof(double);
-  const size_t need = 12 * vec + 2 * red + small;
+  const size_t need = 13 * vec + 2 * red + small;
   if (g->d_solve_bytes < need) {
     if (g->d_solve) cudaFree(g->d_solve);
     g->d_solve = nullptr;
@@ -67,7 +67,7 @@ pspec_status carve(pspec_graph* g, int k, SolveWork<T>* w) {
     g->d_solve_bytes = need;
   }
   char* p = (char*)g->d_solve;
-  T** vecs[12] = {&w->U, &w->Unew, &w->egrad, &w->egrad_new, &w->rg, &w->eta,
+  T** vecs[13] = {&w->U, &w->Unew, &w->egrad, &w->egrad_new, &w->rg, &w->rg_new, &w->eta,
                   &w->Heta, &w->r, &w->delta, &w->He, &w->Hd, &w->tmp};
   for (auto v : vecs) {
     *v = (T*)p;
@@ -85,6 +85,8 @@ pspec_status carve(pspec_graph* g, int k, SolveWork<T>* w) {
   w->F = sm + 1040;
   w->st = (TcgState*)(sm + 1056);
   w->bad = (int*)(sm + 1100);
+  w->Mnew = sm + 1280;
+  w->gdot = sm + 1536;
   w->gr.counters = g->d_counters;
   return PSPEC_OK;
 }
@@ -216,24 +218,32 @@ struct Solver {
     PSPEC_CUDA(cudaGetLastError());
     return PSPEC_OK;
   }
-  // M = U^T egrad, rg = egrad - U M, returns ||rg|| (synchronises)
-  pspec_status riemannian_grad(const T* U, const T* egrad, double* gnorm) {
-    PSPEC_TRY(gram(U, egrad, w.M));
-    PSPEC_TRY(combine(w.rg, egrad, 1.0, nullptr, 0.0, U, w.M, nullptr, nullptr));
+  // M = U^T egrad, rg = egrad - U M and <rg, rg> into *rr (enqueued only)
+  pspec_status riemannian_grad(const T* U, const T* egrad, double* M, T* rg, double* rr) {
+    PSPEC_TRY(gram(U, egrad, M));
+    PSPEC_TRY(combine(rg, egrad, 1.0, nullptr, 0.0, U, M, nullptr, nullptr));
     DotPairs<T> dp{};
-    dp.x[0] = w.rg;
-    dp.y[0] = w.rg;
+    dp.x[0] = rg;
+    dp.y[0] = rg;
     dp.np = 1;
-    PSPEC_TRY(dots(dp, w.dots));
-    double h = 0.0;
-    PSPEC_CUDA(cudaMemcpyAsync(&h, w.dots, sizeof(double), cudaMemcpyDeviceToHost, s));
-    PSPEC_CUDA(cudaStreamSynchronize(s));
-    *gnorm = std::sqrt(std::max(h, 0.0));
-    return PSPEC_OK;
+    return dots(dp, rr);
   }
-  pspec_status read_f(double* f) {
-    PSPEC_CUDA(cudaMemcpyAsync(f, w.F, sizeof(double), cudaMemcpyDeviceToHost, s));
+  // One synchronisation per Newton step: F, the two model dots, <rg, rg> and
+  // the status word land in a pinned host record together.
+  struct Record {
+    double dots[2];
+    double rr;
+    double F;
+    int status;
+  };
+  Record* rec = nullptr;  // pinned, owned by the graph handle
+  pspec_status fetch(bool with_dots) {
+    if (with_dots) PSPEC_CUDA(cudaMemcpyAsync(rec->dots, w.dots, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+    PSPEC_CUDA(cudaMemcpyAsync(&rec->rr, w.gdot, sizeof(double), cudaMemcpyDeviceToHost, s));
+    PSPEC_CUDA(cudaMemcpyAsync(&rec->F, w.F, sizeof(double), cudaMemcpyDeviceToHost, s));
+    PSPEC_CUDA(cudaMemcpyAsync(&rec->status, g->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
     PSPEC_CUDA(cudaStreamSynchronize(s));
+    if (rec->status != 0) PSPEC_CUDA(cudaMemsetAsync(g->d_status, 0, sizeof(int), s));
     return PSPEC_OK;
   }
 };
@@ -254,6 +264,9 @@ static pspec_status solve_impl(pspec_graph* g, int k, const double* sched, int n
   S.alg1 = o.hessian_form == PSPEC_HESSIAN_ALG1;
   PSPEC_TRY(carve<T>(g, k, &S.w));
   SolveWork<T>& w = S.w;
+  if (!g->h_solve_rec) PSPEC_CUDA(cudaMallocHost(&g->h_solve_rec, 512));
+  S.rec = reinterpret_cast<typename Solver<T>::Record*>(g->h_solve_rec);
+  TcgState* st_pinned = reinterpret_cast<TcgState*>(reinterpret_cast<char*>(g->h_solve_rec) + 256);
   const int64_t m = S.m;
   PSPEC_CUDA(cudaMemcpyAsync(w.U, U_io, sizeof(T) * m, cudaMemcpyDeviceToDevice, s));
   PSPEC_CUDA(cudaMemsetAsync(w.bad, 0, sizeof(int), s));
@@ -270,9 +283,11 @@ static pspec_status solve_impl(pspec_graph* g, int k, const double* sched, int n
     const double p = sched[ip];
     double f = 0.0, gnorm = 0.0;
     PSPEC_TRY(S.eval(w.U, p, w.egrad));
-    PSPEC_TRY(S.riemannian_grad(w.U, w.egrad, &gnorm));
-    PSPEC_TRY(S.read_f(&f));
-    PSPEC_TRY(take_status(g, s));
+    PSPEC_TRY(S.riemannian_grad(w.U, w.egrad, w.M, w.rg, w.gdot));
+    PSPEC_TRY(S.fetch(false));
+    PSPEC_TRY(status_error(S.rec->status));
+    f = S.rec->F;
+    gnorm = std::sqrt(std::max(S.rec->rr, 0.0));
     const double gnorm0 = gnorm;
     double Delta = o.delta0_scale * Delta_bar;
     int outer = 0, inner_total = 0;
@@ -327,8 +342,9 @@ static pspec_status solve_impl(pspec_graph* g, int k, const double* sched, int n
         } else {
           PSPEC_TRY(cg_iters(std::min(chunk, o.max_inner - it)));
         }
-        PSPEC_CUDA(cudaMemcpyAsync(&hs, w.st, sizeof(TcgState), cudaMemcpyDeviceToHost, s));
+        PSPEC_CUDA(cudaMemcpyAsync(st_pinned, w.st, sizeof(TcgState), cudaMemcpyDeviceToHost, s));
         PSPEC_CUDA(cudaStreamSynchronize(s));
+        hs = *st_pinned;
         if (hs.done) break;
       }
       S.hvps += hs.j;  // HVP launches enqueued after CG stopped were no-ops
@@ -345,12 +361,13 @@ static pspec_status solve_impl(pspec_graph* g, int k, const double* sched, int n
       dp.y[1] = w.Heta;
       dp.np = 2;
       PSPEC_TRY(S.dots(dp, w.dots));
-      double dv[2] = {0, 0};
-      double f_new = 0.0;
-      PSPEC_CUDA(cudaMemcpyAsync(dv, w.dots, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
-      PSPEC_TRY(S.read_f(&f_new));
+      // the Riemannian gradient at the trial point, used if it is accepted
+      PSPEC_TRY(S.riemannian_grad(w.Unew, w.egrad_new, w.Mnew, w.rg_new, w.gdot));
+      PSPEC_TRY(S.fetch(true));
+      const double dv[2] = {S.rec->dots[0], S.rec->dots[1]};
+      const double f_new = S.rec->F;
       // a trial point whose evaluation met a NaN/Inf or a zero column is rejected
-      const bool trial_bad = take_status(g, s) != PSPEC_OK || !std::isfinite(f_new);
+      const bool trial_bad = S.rec->status != 0 || !std::isfinite(f_new);
       const double reg = o.rho_reg * std::max(1.0, std::fabs(f));
       const double num = f - f_new + reg;
       const double den = -(dv[0] + 0.5 * dv[1]) + reg;
@@ -364,11 +381,13 @@ static pspec_status solve_impl(pspec_graph* g, int k, const double* sched, int n
       if (o.verbose)
         std::fprintf(stderr, "pspec p=%.3f it=%d f=%.10e |g|=%.3e tcg=%d(%d) rho=%.3f Delta=%.3e %s\n", p,
                      outer, f, gnorm, hs.j, hs.reason, rho, Delta, accept ? "acc" : "rej");
-      if (accept) {
+      if (accept) {  // the iterate, its gradient and U^T grad move together
         std::swap(w.U, w.Unew);
         std::swap(w.egrad, w.egrad_new);
+        std::swap(w.M, w.Mnew);
+        std::swap(w.rg, w.rg_new);
         f = f_new;
-        PSPEC_TRY(S.riemannian_grad(w.U, w.egrad, &gnorm));
+        gnorm = std::sqrt(std::max(S.rec->rr, 0.0));
       }
     }
     if (!converged) all_converged = false;
