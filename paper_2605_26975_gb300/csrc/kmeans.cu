@@ -53,6 +53,12 @@ __device__ __forceinline__ double sqdist_row(const T* x, const double* mu, int d
   return acc;
 }
 
+// centre c <- row *idx of X (the index a kernel left in device memory)
+template <typename T>
+__global__ void km_take_row_at(const T* X, int dim, const int64_t* idx, double* centers, int c) {
+  if (threadIdx.x < dim) centers[c * dim + threadIdx.x] = (double)X[(*idx) * dim + threadIdx.x];
+}
+
 // centre c <- row idx of X
 template <typename T>
 __global__ void km_take_row(const T* X, int dim, int64_t idx, double* centers, int c) {
@@ -93,6 +99,9 @@ __global__ void __launch_bounds__(kKmBlock) km_seed_dist(const T* X, int64_t n, 
 // adds the chunk sums in order and walks the one chunk the target falls in
 // row by row.
 constexpr int kPickChunk = 32;
+
+// Lloyd iterations between two host checks of convergence
+constexpr int kKmCheckEvery = 8;
 
 __global__ void __launch_bounds__(kKmBlock) km_pick(const double* d2, const double* block_sum,
                                                     int nblocks, int64_t n, double u,
@@ -185,7 +194,9 @@ __device__ __forceinline__ double km_dist64(const T* xr, const double* mu, int d
 template <typename T>
 __global__ void __launch_bounds__(kKmBlock) km_assign(const T* X, int64_t n, int dim, int C,
                                                       const double* centers, int32_t* labels,
-                                                      double* dmin, unsigned* changed) {
+                                                      double* dmin, unsigned* changed,
+                                                      const unsigned* done) {
+  if (*done) return;
   __shared__ double mu[kKmMaxC * kKmMaxDim];
   __shared__ float mu32[kKmMaxC * kKmMaxDim];
   __shared__ float nmu[kKmMaxC];  // |mu_c|, rounded up
@@ -250,7 +261,9 @@ __global__ void __launch_bounds__(kKmBlock) km_assign(const T* X, int64_t n, int
 // warp w owns clusters w, w+8, ...; its lanes stride the block's rows
 template <typename T>
 __global__ void __launch_bounds__(kKmBlock) km_partial(const T* X, int64_t n, int dim, int C,
-                                                       const int32_t* labels, double* part) {
+                                                       const int32_t* labels, double* part,
+                                                       const unsigned* done) {
+  if (*done) return;
   const int64_t per = (n + gridDim.x - 1) / gridDim.x;
   const int64_t b0 = blockIdx.x * per, b1 = min(n, b0 + per);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -274,7 +287,8 @@ __global__ void __launch_bounds__(kKmBlock) km_partial(const T* X, int64_t n, in
 
 // centres = sums / counts (blocks summed in order); counts to host-visible array
 __global__ void km_finish(const double* part, int nblocks, int C, int dim, double* centers,
-                          double* counts) {
+                          double* counts, const unsigned* done) {
+  if (*done) return;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= C * (dim + 1)) return;
   double acc = 0.0;
@@ -290,34 +304,54 @@ __global__ void km_finish(const double* part, int nblocks, int C, int dim, doubl
   }
 }
 
-// argmax of dmin (first maximum), one block: per-thread strided scan then tree
-__global__ void km_argmax(double* dmin, int64_t n, int64_t* out_idx) {
+// Empty clusters, in cluster order: each takes the row farthest from its own
+// old centre (dmin, first maximum) as its centre, and that row is excluded
+// from the next one (dmin = -1).  One block; returns at once when no cluster
+// is empty.
+template <typename T>
+__global__ void km_reseed(const T* X, int64_t n, int dim, int C, const double* counts, double* dmin,
+                          double* centers, const unsigned* done) {
   __shared__ double sv[kKmBlock];
   __shared__ int64_t si[kKmBlock];
-  double bv = -1.0;
-  int64_t bi = n;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    const double v = dmin[i];
-    if (v > bv) { bv = v; bi = i; }
-  }
-  sv[threadIdx.x] = bv;
-  si[threadIdx.x] = bi;
-  __syncthreads();
-  for (int h = kKmBlock / 2; h > 0; h >>= 1) {
-    if (threadIdx.x < h) {
-      const double ov = sv[threadIdx.x + h];
-      const int64_t oi = si[threadIdx.x + h];
-      if (ov > sv[threadIdx.x] || (ov == sv[threadIdx.x] && oi < si[threadIdx.x])) {
-        sv[threadIdx.x] = ov;
-        si[threadIdx.x] = oi;
+  if (*done) return;
+  for (int c = 0; c < C; ++c) {
+    if (counts[c] != 0.0) continue;  // uniform over the block
+    double bv = -1.0;
+    int64_t bi = n;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const double v = dmin[i];
+      if (v > bv) { bv = v; bi = i; }
+    }
+    sv[threadIdx.x] = bv;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int h = kKmBlock / 2; h > 0; h >>= 1) {
+      if (threadIdx.x < h) {
+        const double ov = sv[threadIdx.x + h];
+        const int64_t oi = si[threadIdx.x + h];
+        if (ov > sv[threadIdx.x] || (ov == sv[threadIdx.x] && oi < si[threadIdx.x])) {
+          sv[threadIdx.x] = ov;
+          si[threadIdx.x] = oi;
+        }
       }
+      __syncthreads();
+    }
+    const int64_t far = si[0];
+    if (far < n) {
+      if (threadIdx.x < dim) centers[c * dim + threadIdx.x] = (double)X[far * dim + threadIdx.x];
+      __syncthreads();
+      if (threadIdx.x == 0) dmin[far] = -1.0;
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    *out_idx = si[0];
-    if (si[0] < n) dmin[si[0]] = -1.0;  // exclude it from the next re-seed
-  }
+}
+
+// end of a Lloyd iteration: an assignment that changed no label is a fixed
+// point, and every later iteration leaves the state as it is (done = 1).
+__global__ void km_mark(unsigned* changed, unsigned* done) {
+  if (*done) return;
+  if (*changed == 0) *done = 1;
+  *changed = 0;
 }
 
 __global__ void km_sum(const double* v, int64_t n, double* out) {
@@ -342,7 +376,7 @@ struct KmWork {
   double* counts;
   int32_t* labels;
   int64_t* idx;
-  unsigned* changed;
+  unsigned* changed;  // [0] labels changed by the last assignment, [1] done
   double* scalar;
   int nblocks;
 };
@@ -374,7 +408,6 @@ static pspec_status kmeans_impl(const T* X, int64_t n, int dim, int C, uint64_t 
   w.labels = (int32_t*)carve(sizeof(int32_t) * n);
   w.idx = (int64_t*)carve(sizeof(int64_t) * 2);
   w.changed = (unsigned*)carve(sizeof(unsigned) * 2);
-  std::vector<double> counts(C);
   SplitMix64 rng(seed);
   double best = INFINITY;
   pspec_status st = PSPEC_OK;
@@ -389,41 +422,36 @@ static pspec_status kmeans_impl(const T* X, int64_t n, int dim, int C, uint64_t 
       for (int c = 1; c < C; ++c) {
         const double uc = rng.uniform();
         km_pick<<<1, kKmBlock, 0, s>>>(w.d2, w.part, w.nblocks, n, uc, w.idx);
-        int64_t idx = 0;
-        cudaMemcpyAsync(&idx, w.idx, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-        cudaError_t e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) { st = cuda_error(e, "kmeans seeding"); break; }
-        km_take_row<T><<<1, 32, 0, s>>>(X, dim, idx, w.centers, c);
+        km_take_row_at<T><<<1, 32, 0, s>>>(X, dim, w.idx, w.centers, c);
         km_seed_dist<T><<<w.nblocks, kKmBlock, 0, s>>>(X, n, dim, w.centers, c, 0, w.d2, w.part);
       }
     }
     if (st != PSPEC_OK) break;
-    // ---- Lloyd
+    // ---- Lloyd.  The iterations run in chunks with one host check each: a
+    // converged state is marked done on the device and the rest of the chunk
+    // skips, so the result is the one of checking after every iteration.
     cudaMemsetAsync(w.labels, 0xff, sizeof(int32_t) * n, s);  // -1: every label "changes"
+    cudaMemsetAsync(w.changed, 0, sizeof(unsigned) * 2, s);
+    km_assign<T><<<ab, kKmBlock, 0, s>>>(X, n, dim, C, w.centers, w.labels, w.dmin, w.changed, w.changed + 1);
     cudaMemsetAsync(w.changed, 0, sizeof(unsigned), s);
-    km_assign<T><<<ab, kKmBlock, 0, s>>>(X, n, dim, C, w.centers, w.labels, w.dmin, w.changed);
-    for (int it = 0; it < max_iter; ++it) {
-      km_partial<T><<<w.nblocks, kKmBlock, 0, s>>>(X, n, dim, C, w.labels, w.part);
-      km_finish<<<(C * (dim + 1) + 127) / 128, 128, 0, s>>>(w.part, w.nblocks, C, dim, w.centers, w.counts);
-      cudaMemcpyAsync(counts.data(), w.counts, sizeof(double) * C, cudaMemcpyDeviceToHost, s);
-      cudaError_t e = cudaStreamSynchronize(s);
-      if (e != cudaSuccess) { st = cuda_error(e, "kmeans update"); break; }
-      for (int c = 0; c < C; ++c) {
-        if (counts[c] == 0.0) {  // empty: re-seed at the farthest row (dmin = old distances)
-          km_argmax<<<1, kKmBlock, 0, s>>>(w.dmin, n, w.idx + 1);
-          int64_t far = 0;
-          cudaMemcpyAsync(&far, w.idx + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-          cudaStreamSynchronize(s);
-          km_take_row<T><<<1, 32, 0, s>>>(X, dim, far, w.centers, c);
-        }
+    for (int it = 0; it < max_iter;) {
+      const int chunk = std::min(kKmCheckEvery, max_iter - it);
+      for (int q = 0; q < chunk; ++q) {
+        km_partial<T><<<w.nblocks, kKmBlock, 0, s>>>(X, n, dim, C, w.labels, w.part, w.changed + 1);
+        km_finish<<<(C * (dim + 1) + 127) / 128, 128, 0, s>>>(w.part, w.nblocks, C, dim, w.centers, w.counts,
+                                                               w.changed + 1);
+        // empty clusters re-seed at the farthest rows (dmin = distances to the old centres)
+        km_reseed<T><<<1, kKmBlock, 0, s>>>(X, n, dim, C, w.counts, w.dmin, w.centers, w.changed + 1);
+        km_assign<T><<<ab, kKmBlock, 0, s>>>(X, n, dim, C, w.centers, w.labels, w.dmin, w.changed,
+                                             w.changed + 1);
+        km_mark<<<1, 1, 0, s>>>(w.changed, w.changed + 1);
       }
-      unsigned changed = 0;
-      cudaMemsetAsync(w.changed, 0, sizeof(unsigned), s);
-      km_assign<T><<<ab, kKmBlock, 0, s>>>(X, n, dim, C, w.centers, w.labels, w.dmin, w.changed);
-      cudaMemcpyAsync(&changed, w.changed, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
-      e = cudaStreamSynchronize(s);
-      if (e != cudaSuccess) { st = cuda_error(e, "kmeans assign"); break; }
-      if (changed == 0) break;
+      it += chunk;
+      unsigned done = 0;
+      cudaMemcpyAsync(&done, w.changed + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+      cudaError_t e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) { st = cuda_error(e, "kmeans Lloyd"); break; }
+      if (done) break;
     }
     if (st != PSPEC_OK) break;
     km_sum<<<1, kKmBlock, 0, s>>>(w.dmin, n, w.scalar);

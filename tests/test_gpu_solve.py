@@ -56,6 +56,34 @@ def test_kmeans_empty_cluster_and_duplicates(api):
     assert inertia == ref_inertia == 0.0
 
 
+@pytest.mark.parametrize("max_iter", [0, 1, 3, 8, 9, 17, 300])
+def test_kmeans_iteration_cap(api, max_iter):
+    # overlapping blobs converge slowly, so most caps stop Lloyd before a
+    # fixed point, at every offset inside a chunk of device-side iterations
+    X = blobs(11, 6000, 3, 6, spread=0.8)
+    lab, cent, inertia = api.kmeans(torch.from_numpy(X).cuda(), 6, seed=5, restarts=2, max_iter=max_iter)
+    ref_lab, ref_cent, ref_inertia = oracle.kmeans(X.astype(np.float64), 6, seed=5, restarts=2,
+                                                   max_iter=max_iter)
+    assert np.array_equal(lab.cpu().numpy(), ref_lab)
+    assert abs(inertia - ref_inertia) <= 1e-10 * ref_inertia
+    assert np.allclose(cent.cpu().numpy(), ref_cent, rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("seed,max_iter", [(1, 1), (2, 2), (3, 9), (4, 300)])
+def test_kmeans_more_clusters_than_points(api, seed, max_iter):
+    # 3 distinct rows, 5 clusters: seeding repeats rows, the repeated centres
+    # stay empty and are re-seeded at the farthest rows while no label
+    # changes -- Lloyd must still stop at that first unchanged assignment
+    X = np.repeat(np.array([[0, 0], [2, 0], [0, 3]], dtype=np.float32), [7, 5, 9], axis=0)
+    lab, cent, inertia = api.kmeans(torch.from_numpy(X).cuda(), 5, seed=seed, restarts=2,
+                                    max_iter=max_iter)
+    ref_lab, ref_cent, ref_inertia = oracle.kmeans(X.astype(np.float64), 5, seed=seed, restarts=2,
+                                                   max_iter=max_iter)
+    assert np.array_equal(lab.cpu().numpy(), ref_lab)
+    assert inertia == ref_inertia
+    assert np.array_equal(cent.cpu().numpy(), ref_cent)
+
+
 def test_rcut_matches_oracle(api):
     g = wl.sbm_sampled(np.random.default_rng(2), 5000, 5, 12.0, 0.8)
     G = api.Graph.from_csr(g)
