@@ -185,6 +185,10 @@ pspec_status eval_fast(pspec_graph* g, const float* U, int k, double p, double* 
                        float* grad, double* parts, cudaStream_t s);
 pspec_status hvp_fast(pspec_graph* g, const float* U, const float* V, int k, double p, float* HV,
                       cudaStream_t s, const int* skip = nullptr, bool alg1 = false);
+// the edge kernel of hvp_fast alone: S (sparse part) into S, Delta_p u into
+// the handle's scratch block, the epilogue coefficients into d_scalars
+pspec_status hvp_edges_fast(pspec_graph* g, const float* U, const float* V, int k, double p, float* S,
+                            cudaStream_t s, const int* skip = nullptr, bool alg1 = false);
 
 // batches: per-graph scalars, 128 doubles per graph in d_graph_scalars
 constexpr int kGsN = 0, kGsD = 16, kGsC0 = 32, kGsC1 = 48, kGsC2 = 64, kGsC3 = 80, kGsC4 = 96,

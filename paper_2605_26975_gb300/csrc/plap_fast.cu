@@ -6,6 +6,7 @@
 #include <cstring>
 
 #include "common.cuh"
+#include "epilogue.cuh"
 #include "internal.h"
 
 namespace pspec {
@@ -124,11 +125,9 @@ __global__ void __launch_bounds__(256) hvp_epilogue(const float* __restrict__ U,
     const int c = (int)((v * VW) % K);
 #pragma unroll
     for (int j = 0; j < VW; ++j) {
-      float su = abs_pow_pm2_clamped(u[j], pm2);
-      const float phu = su * u[j];
-      if (zero_rule && u[j] == 0.0f) su = 0.0f;
       const int cc = c + j;
-      s[j] = sA[cc] * (s[j] - sL[cc] * su * x[j]) - sB[cc] * (dl[j] * sSD[cc] + phu * sE[cc]);
+      const HvpCoef cf{sA[cc], sL[cc], sB[cc], sSD[cc], sE[cc]};
+      s[j] = hvp_entry(s[j], u[j], x[j], dl[j], cf, pm2, zero_rule);
     }
     store_vec<VW>(HV + v * VW, s);
   }
@@ -174,13 +173,18 @@ static pspec_status ensure_scratch(pspec_graph* g, size_t elems) {
   return PSPEC_OK;
 }
 
+pspec_status hvp_edges_fast(pspec_graph* g, const float* U, const float* V, int k, double p, float* S,
+                            cudaStream_t s, const int* skip, bool alg1) {
+  PSPEC_TRY(ensure_scratch(g, (size_t)g->n * k));
+  EdgeLaunch L{U, V, S, g->d_scratch, (float)p, k, skip};
+  L.alg1 = alg1;
+  return launch_hvp_edges(g, L, s);
+}
+
 pspec_status hvp_fast(pspec_graph* g, const float* U, const float* V, int k, double p, float* HV,
                       cudaStream_t s, const int* skip, bool alg1) {
   const int64_t ne = g->n * k;
-  PSPEC_TRY(ensure_scratch(g, (size_t)ne));
-  EdgeLaunch L{U, V, HV, g->d_scratch, (float)p, k, skip};
-  L.alg1 = alg1;
-  PSPEC_TRY(launch_hvp_edges(g, L, s));
+  PSPEC_TRY(hvp_edges_fast(g, U, V, k, p, HV, s, skip, alg1));
   const float pm2 = (float)p - 2.0f;
   TimedScope timer(g, "hvp_epilogue", s);
   if (k % 4 == 0)
@@ -312,11 +316,9 @@ __global__ void __launch_bounds__(256) hvp_epilogue_b(const float* __restrict__ 
 #pragma unroll
     for (int jj = 0; jj < VW; ++jj) {
       const int cc = c + jj;
-      float su = abs_pow_pm2_clamped(u[jj], pm2);
-      const float phu = su * u[jj];
-      if (zero_rule && u[jj] == 0.0f) su = 0.0f;
-      sv[jj] = (float)g[kGsC0 + cc] * (sv[jj] - (float)g[kGsC1 + cc] * su * x[jj]) -
-               (float)g[kGsC2 + cc] * (dl[jj] * (float)g[kGsC3 + cc] + phu * (float)g[kGsC4 + cc]);
+      const HvpCoef cf{(float)g[kGsC0 + cc], (float)g[kGsC1 + cc], (float)g[kGsC2 + cc],
+                       (float)g[kGsC3 + cc], (float)g[kGsC4 + cc]};
+      sv[jj] = hvp_entry(sv[jj], u[jj], x[jj], dl[jj], cf, pm2, zero_rule);
     }
     store_vec<VW>(HV + e0, sv);
   }

@@ -153,6 +153,22 @@ struct Solver {
     else
       return hvp_plain64(g, U, V, k, p, out, s, alg1);
   }
+  // Hv = H[V] and Gm = U^T Hv: for FP32 with k a multiple of 4 the epilogue
+  // and the Gram product run as one kernel (same bits as the two calls)
+  pspec_status hvp_gram(const T* U, const T* V, double p, T* Hv, double* Gm, const int* done) {
+    if constexpr (sizeof(T) == 4) {
+      if (k % 4 == 0) {
+        PSPEC_TRY(hvp_edges_fast(g, U, V, k, p, Hv, s, done, alg1));
+        TimedScope timer(g, "hvp_epi_gram", s);
+        hvp_epi_gram_kernel<<<w.tblocks, kSolveBlock, 0, s>>>(U, V, g->d_scratch, Hv, n, k, g->d_scalars,
+                                                              (float)p - 2.0f, Gm, w.gr, done);
+        PSPEC_CUDA(cudaGetLastError());
+        return PSPEC_OK;
+      }
+    }
+    PSPEC_TRY(hvp(U, V, p, Hv, done));
+    return gram(U, Hv, Gm, done);
+  }
   pspec_status gram(const T* A, const T* B, double* G, const int* done = nullptr) {
     TimedScope timer(g, "solve_gram", s);
     if constexpr (sizeof(T) == 4) {
@@ -319,8 +335,7 @@ static pspec_status solve_impl(pspec_graph* g, int k, const double* sched, int n
       // Hessian and the CG updates, all decided on the device
       auto cg_iters = [&](int count) -> pspec_status {
         for (int c = 0; c < count; ++c) {
-          PSPEC_TRY(S.hvp(w.U, w.delta, p, w.He, done));
-          PSPEC_TRY(S.gram(w.U, w.He, w.G, done));
+          PSPEC_TRY(S.hvp_gram(w.U, w.delta, p, w.He, w.G, done));
           TimedScope timer(g, "solve_tcg_vec", s);
           S.hess(w.st);
           cg_update_kernel<T><<<w.vblocks, kSolveBlock, 0, s>>>(w.eta, w.Heta, w.r, w.delta,

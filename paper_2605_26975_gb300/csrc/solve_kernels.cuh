@@ -10,6 +10,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "epilogue.cuh"
 
 namespace pspec {
 
@@ -376,6 +377,129 @@ __global__ void __launch_bounds__(kSolveBlock) gram_tma_kernel(const float* __re
   if (!grid_reduce_rt<R>(s_blk, s_tot, nv, gr)) return;
   for (int q = threadIdx.x; q < nv; q += kSolveBlock) G[q] = red_to_double(s_tot[q]);
 }
+
+// The fast path's HVP epilogue fused with G = U^T HV (k a multiple of 4), the
+// two products truncated CG needs back to back.  The grid, the order of the
+// tiles and the 4 x 4 output blocks of the threads are those of
+// gram_tma_kernel, and every HV entry is hvp_entry's, so HV and G equal the
+// two-kernel result bit for bit; the U and HV rows of a tile come into shared
+// memory from the epilogue's own loads instead of being read again.  A block
+// stages kEpiTiles tiles per step (more loads in flight per thread).  S (the
+// edge kernel's sparse part) is read from HV and overwritten.
+constexpr int kEpiTiles = 2;
+
+__global__ void __launch_bounds__(kSolveBlock, 3) hvp_epi_gram_kernel(
+    const float* __restrict__ U, const float* __restrict__ V, const float* __restrict__ Dl, float* HV,
+    int64_t n, int k, const double* __restrict__ scalars, float pm2, double* G, GridRed gr,
+    const int* done) {
+  using R = float2;
+  if (done && *done) return;
+  __shared__ __align__(16) float tiles[kEpiTiles * 2 * kGramTileFloats];  // [tile][U | HV]
+  __shared__ HvpCoef coef[kMaxK];
+  __shared__ R s_blk[kMaxK * kMaxK];
+  __shared__ R s_tot[kMaxK * kMaxK];
+  const int t = threadIdx.x;
+  if (t < k) {
+    const double* c = scalars + kSlotCoef;
+    coef[t] = HvpCoef{(float)c[t], (float)c[16 + t], (float)c[32 + t], (float)c[48 + t], (float)c[64 + t]};
+  }
+  const bool zero_rule = pm2 != 0.0f;
+  const int nv = k * k;
+  const int nb = k / 4;
+  const int nblk = nb * nb;
+  const int groups = kSolveBlock / nblk;
+  const int pb = t % nblk, grp = t / nblk;
+  const bool worker = grp < groups;
+  const int a0 = 4 * (pb / nb), b0 = 4 * (pb % nb);
+  const int64_t nfull = n / kGramTile;
+  const int rows_last = (int)(n - nfull * kGramTile);
+  const int64_t ntiles = nfull + (rows_last > 0 ? 1 : 0);
+  Kahan acc[16];
+  float part[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    acc[q].init();
+    part[q] = 0.f;
+  }
+  int it = 0;  // full tiles of this block accumulated so far
+  for (int64_t base = blockIdx.x; base < ntiles; base += (int64_t)kEpiTiles * gridDim.x) {
+    __syncthreads();  // coefficients staged; the previous step's tiles consumed
+    for (int q = 0; q < kEpiTiles; ++q) {
+      const int64_t tile = base + (int64_t)q * gridDim.x;
+      if (tile >= ntiles) break;
+      const int rows = tile < nfull ? kGramTile : rows_last;
+      const int cv = rows * k / 4;
+      float4* su = reinterpret_cast<float4*>(tiles + (size_t)q * 2 * kGramTileFloats);
+      float4* sh = su + kGramTileFloats / 4;
+      const int64_t e0 = tile * kGramTile * k / 4;  // first float4 of the tile
+      for (int e = t; e < cv; e += kSolveBlock) {
+        const float4 u = __ldg(reinterpret_cast<const float4*>(U) + e0 + e);
+        const float4 x = __ldg(reinterpret_cast<const float4*>(V) + e0 + e);
+        const float4 dl = __ldg(reinterpret_cast<const float4*>(Dl) + e0 + e);
+        const float4 sv = reinterpret_cast<const float4*>(HV)[e0 + e];
+        const int c = (e * 4) % k;
+        float4 h;
+        h.x = hvp_entry(sv.x, u.x, x.x, dl.x, coef[c], pm2, zero_rule);
+        h.y = hvp_entry(sv.y, u.y, x.y, dl.y, coef[c + 1], pm2, zero_rule);
+        h.z = hvp_entry(sv.z, u.z, x.z, dl.z, coef[c + 2], pm2, zero_rule);
+        h.w = hvp_entry(sv.w, u.w, x.w, dl.w, coef[c + 3], pm2, zero_rule);
+        reinterpret_cast<float4*>(HV)[e0 + e] = h;
+        su[e] = u;
+        sh[e] = h;
+      }
+    }
+    __syncthreads();
+    for (int q = 0; q < kEpiTiles; ++q) {
+      const int64_t tile = base + (int64_t)q * gridDim.x;
+      if (tile >= ntiles) break;
+      const int rows = tile < nfull ? kGramTile : rows_last;
+      const float* sa = tiles + (size_t)q * 2 * kGramTileFloats;
+      const float* sb = sa + kGramTileFloats;
+      if (worker) {
+        for (int r = grp; r < rows; r += groups) {
+          const float4 av = *reinterpret_cast<const float4*>(sa + r * k + a0);
+          const float4 bv = *reinterpret_cast<const float4*>(sb + r * k + b0);
+          const float aa[4] = {av.x, av.y, av.z, av.w};
+          const float bb[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) part[i * 4 + j] = fmaf(aa[i], bb[j], part[i * 4 + j]);
+        }
+        if (tile < nfull && (it & 3) == 3) {
+#pragma unroll
+          for (int w = 0; w < 16; ++w) {
+            acc[w].add(part[w]);
+            part[w] = 0.f;
+          }
+        }
+      }
+      if (tile < nfull) ++it;
+    }
+  }
+  if (worker) {
+#pragma unroll
+    for (int w = 0; w < 16; ++w) acc[w].add(part[w]);
+  }
+  // the row groups of each output entry in order, as gram_tma_kernel
+  __syncthreads();
+  float2* s_part = reinterpret_cast<float2*>(tiles);  // [16][kSolveBlock]
+#pragma unroll
+  for (int q = 0; q < 16; ++q) s_part[q * kSolveBlock + t] = worker ? kahan_to_ff(acc[q]) : make_float2(0.f, 0.f);
+  __syncthreads();
+  if (t < nv) {
+    const int a = t / k, b = t - (t / k) * k;
+    const int blk = (a / 4) * nb + (b / 4), q = (a % 4) * 4 + (b % 4);
+    R sum = make_float2(0.f, 0.f);
+    for (int g2 = 0; g2 < groups; ++g2) sum = red_add(sum, s_part[q * kSolveBlock + g2 * nblk + blk]);
+    s_blk[t] = sum;
+  }
+  __syncthreads();
+  if (!grid_reduce_rt<R>(s_blk, s_tot, nv, gr)) return;
+  for (int q = threadIdx.x; q < nv; q += kSolveBlock) G[q] = red_to_double(s_tot[q]);
+}
+static_assert(sizeof(float) * kEpiTiles * 2 * kGramTileFloats >= sizeof(float2) * 16 * kSolveBlock,
+              "the staged tiles hold the per-thread partial sums at the end");
 
 // k rounded up to the register-array width the row kernels are built for
 __host__ __device__ constexpr int k_bucket(int k) { return k <= 4 ? 4 : k <= 8 ? 8 : 16; }
