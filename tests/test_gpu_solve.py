@@ -56,6 +56,27 @@ def test_kmeans_empty_cluster_and_duplicates(api):
     assert inertia == ref_inertia == 0.0
 
 
+@pytest.mark.parametrize("scale", [1e-30, 1e-3, 1e3, 1e30])
+def test_kmeans_row_magnitudes(api, scale):
+    # the member sums of FP32 rows are exact fixed-point sums scaled by
+    # 2^q from max |x|: large q, negative q, and rows too small for a finite
+    # scale (the FP64 sums) all agree with the oracle
+    X = (blobs(3, 4000, 8, 5) * np.float32(scale)).astype(np.float32)
+    lab, cent, inertia = api.kmeans(torch.from_numpy(X).cuda(), 5, seed=2, restarts=2, max_iter=60)
+    ref_lab, ref_cent, ref_inertia = oracle.kmeans(X.astype(np.float64), 5, seed=2, restarts=2,
+                                                   max_iter=60)
+    assert np.array_equal(lab.cpu().numpy(), ref_lab)
+    assert abs(inertia - ref_inertia) <= 1e-10 * ref_inertia
+    assert np.allclose(cent.cpu().numpy(), ref_cent, rtol=1e-10, atol=1e-12 * scale)
+
+
+def test_kmeans_rejects_non_finite_rows(api):
+    X = blobs(4, 500, 4, 3)
+    X[17, 2] = np.nan
+    with pytest.raises(api._abi.PspecError, match="NaN"):
+        api.kmeans(torch.from_numpy(X).cuda(), 3)
+
+
 @pytest.mark.parametrize("max_iter", [0, 1, 3, 8, 9, 17, 300])
 def test_kmeans_iteration_cap(api, max_iter):
     # overlapping blobs converge slowly, so most caps stop Lloyd before a

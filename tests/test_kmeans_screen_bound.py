@@ -57,6 +57,26 @@ def test_screen_bound_holds(dim):
     assert worst < 1.0
 
 
+@pytest.mark.parametrize("dim", [2, 8, 16])
+def test_screen_bound_in_the_subnormal_range(dim):
+    """Rows and centres near 1e-21: the FP32 squares and sums fall into the
+    subnormal range, where rounding is absolute (at most dim 2^-149 in all),
+    and only the bound's 2^-120 floor covers them (the relative terms alone
+    would not)."""
+    rng = np.random.default_rng(100 + dim)
+    floor_needed = False
+    for trial in range(3000):
+        scale = 10.0 ** rng.uniform(-25, -18)
+        mu = rng.standard_normal(dim) * scale
+        x = (mu + rng.standard_normal(dim) * scale).astype(np.float32)
+        d32, d64 = d32_of(x, mu), d64_of(x, mu)
+        nmu = float(np.sqrt(np.sum(mu * mu)) * (1 + 1e-6))
+        hb = half_bound(d32, nmu, dim)
+        assert abs(d32 - d64) <= hb + 2.0 ** -121, (trial, d32, d64, hb)
+        floor_needed |= abs(d32 - d64) > hb
+    assert floor_needed  # the case the floor is there for does occur
+
+
 def test_screen_separates_clear_rows_only():
     """A clearly nearer centre passes the screen; an exact FP64 tie never
     does (the FP64 loop then decides, ties to the smaller centre)."""
