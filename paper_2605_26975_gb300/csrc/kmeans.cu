@@ -16,11 +16,13 @@
 //    cluster re-seeded (in cluster order) at the row farthest from its
 //    centre, stop when no label changes or after max_iter updates;
 //  * restarts: the smallest inertia wins (the first on ties).
-// All reductions have a fixed order; only integer counters use atomics.
+// The means of FP32 rows are exact fixed-point sums (integer atomics, so
+// order-free) scaled back by a power of two; every floating-point reduction
+// has a fixed order, so results are reproducible run to run.
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
-#include <cmath>
 #include <vector>
 
 #include "common.cuh"
