@@ -47,6 +47,20 @@ def test_kmeans_matches_oracle(api, n, dim, C, dtype):
     assert np.allclose(cent.cpu().numpy(), ref_cent, rtol=1e-10, atol=1e-12)
 
 
+@pytest.mark.parametrize("n,dim,C,dtype", [(4000, 16, 64, np.float32), (64, 1, 64, np.float32),
+                                           (3000, 5, 7, np.float32), (2500, 16, 64, np.float64)])
+def test_kmeans_extreme_shapes(api, n, dim, C, dtype):
+    # the most clusters, as many clusters as rows, a row width off the
+    # register buckets (one load per entry), and FP64 rows with 64 clusters
+    X = blobs(n * 7 + C, n, dim, C, spread=0.3, dtype=dtype)
+    lab, cent, inertia = api.kmeans(torch.from_numpy(X).cuda(), C, seed=11, restarts=2, max_iter=50)
+    ref_lab, ref_cent, ref_inertia = oracle.kmeans(X.astype(np.float64), C, seed=11, restarts=2,
+                                                   max_iter=50)
+    assert np.array_equal(lab.cpu().numpy(), ref_lab)
+    assert abs(inertia - ref_inertia) <= 1e-10 * max(ref_inertia, 1e-300)
+    assert np.allclose(cent.cpu().numpy(), ref_cent, rtol=1e-10, atol=1e-12)
+
+
 def test_kmeans_empty_cluster_and_duplicates(api):
     # heavy duplicates: k-means++ can only pick distinct rows when D^2 > 0
     X = np.repeat(np.array([[0, 0], [1, 0], [0, 1], [5, 5]], dtype=np.float32), 50, axis=0)
