@@ -220,11 +220,11 @@ pspec_status na_scratch(void** out) {
 
 template <int K>
 pspec_status na_launch(const NaArgs& a, int sm_count, cudaStream_t s) {
-  static int occ = -1;
-  if (occ < 0) {
-    PSPEC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, na_hvp_edges<K>, kBlock, 0));
-    occ = std::max(occ, 1);
-  }
+  static const int occ = [] {  // once per instantiation, thread-safe
+    int o = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, na_hvp_edges<K>, kBlock, 0) != cudaSuccess) o = 1;
+    return std::max(o, 1);
+  }();
   constexpr int RPW = 32 / (kNaEdgeSlots * q_of(K));
   const int64_t want = (a.n + (int64_t)RPW * kWarps - 1) / ((int64_t)RPW * kWarps);
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>({want, (int64_t)sm_count * occ, kNaMaxBlocks}));

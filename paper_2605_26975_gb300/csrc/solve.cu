@@ -177,12 +177,10 @@ struct Solver {
         PSPEC_CUDA(cudaGetLastError());
         return PSPEC_OK;
       }
-      static bool attr = false;
-      if (!attr) {
-        PSPEC_CUDA(cudaFuncSetAttribute(gram_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)gram_tma_smem_bytes()));
-        attr = true;
-      }
+      // once per process, thread-safe (batched solves run on several host threads)
+      static const cudaError_t attr = cudaFuncSetAttribute(
+          gram_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_tma_smem_bytes());
+      PSPEC_CUDA(attr);
       gram_tma_kernel<<<w.tblocks, kSolveBlock, gram_tma_smem_bytes(), s>>>(A, B, n, k, G, w.gr, done,
                                                                              g->d_status);
     } else {
