@@ -4,8 +4,11 @@ The p = 2 stage is pinned by the Ky Fan theorem: over orthonormal n x k
 blocks, F_2 = trace(U^T L U) is minimised by the k smallest eigenvectors of
 the graph Laplacian, so the solve must reach the sum of the k smallest
 eigenvalues (closed forms on the path and the cycle, a dense symmetric
-eigensolver on random graphs).  The p < 2 stages have no closed form ("parity
-unpinned"); they are checked for descent and planted-block recovery only.
+eigensolver on random graphs).  At p < 2 the Newton model is pinned by its
+parts: the Riemannian Hessian against central differences of the projected
+gradient, truncated CG against the Cauchy decrease it guarantees.  The p < 2
+trajectory itself has no closed form ("parity unpinned"); it is checked for
+descent and planted-block recovery only.
 """
 import math
 
@@ -89,6 +92,66 @@ def test_riemannian_hessian_is_tangent():
     eg = oracle.euclidean_grad(g, U, 1.5)
     H = oracle.riemannian_hessian(U, eg, oracle.euclidean_hvp(g, U, eta, 1.5), eta)
     assert np.allclose(U.T @ H, 0, atol=1e-12)
+
+
+@pytest.mark.parametrize("p", [1.3, 1.6, 2.0])
+def test_riemannian_hessian_is_derivative_of_projected_gradient(p):
+    """For tangent eta, differentiating X -> (I - X X^T) grad F(X) at X = U
+    along eta gives (I - U U^T) H eta - (eta U^T + U eta^T) grad F; the
+    tangent projection of that is P_U(H eta) - eta (U^T grad F), the
+    Riemannian Hessian the solve uses.  Central differences of the Euclidean
+    gradient check it (the Weingarten term's sign included) at p < 2, where
+    nothing else pins the Newton model."""
+    rng = np.random.default_rng(int(p * 10))
+    n, k = 25, 3
+    A = np.triu((rng.random((n, n)) < 0.3) * rng.uniform(0.5, 1.5, (n, n)), 1)
+    g = dense_graph(A + A.T)
+    U = oracle.qf(rng.standard_normal((n, k)))
+    eta = oracle.project(U, rng.standard_normal((n, k)))
+
+    def field(X):
+        return oracle.euclidean_grad(g, X, p) - X @ (X.T @ oracle.euclidean_grad(g, X, p))
+
+    def central(t):
+        return (field(U + t * eta) - field(U - t * eta)) / (2 * t)
+
+    # Richardson: |d|^p has a large third derivative where an edge's
+    # difference is small, so cancel the central difference's t^2 term
+    # (the smallest |u| and edge difference here are ~6e-4)
+    t = 1e-6
+    fd = oracle.project(U, (4 * central(t / 2) - central(t)) / 3)
+    egrad = oracle.euclidean_grad(g, U, p)
+    H = oracle.riemannian_hessian(U, egrad, oracle.euclidean_hvp(g, U, eta, p), eta)
+    assert np.allclose(H, fd, rtol=1e-7, atol=1e-8 * np.abs(H).max())
+    # a flipped curvature term would be far off
+    wrong = oracle.project(U, oracle.euclidean_hvp(g, U, eta, p)) + eta @ (U.T @ egrad)
+    assert not np.allclose(wrong, fd, rtol=1e-3, atol=1e-4 * np.abs(H).max())
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_tcg_model_no_worse_than_cauchy_point(seed):
+    """Steihaug-Toint truncated CG takes the Cauchy point -tau g (the model's
+    minimiser along -g inside the radius) as its first iterate and never
+    raises the model afterwards, so it ends at or below the Cauchy point's
+    model value, inside the trust region."""
+    rng = np.random.default_rng(40 + seed)
+    m = 15
+    B = rng.standard_normal((m, m))
+    A = B @ B.T / m + (rng.uniform(-1.0, 0.5) if seed % 2 else 0.1) * np.eye(m)  # odd seeds: indefinite
+    g = rng.standard_normal((m, 1))
+    Delta = 10.0 ** rng.uniform(-1.5, 1.0)
+
+    def model(x):
+        return (g.T @ x + 0.5 * x.T @ A @ x).item()
+
+    gAg = (g.T @ A @ g).item()
+    gn = float(np.linalg.norm(g))
+    tau = Delta / gn if gAg <= 0 else min(gn * gn / gAg, Delta / gn)
+    m_cauchy = model(-tau * g)
+    eta, Heta, its, reason, boundary = oracle.tcg(lambda x: A @ x, g, Delta, 1.0, 0.01, 100)
+    assert np.linalg.norm(eta) <= Delta * (1 + 1e-12)
+    assert model(eta) <= m_cauchy + 1e-12 * abs(m_cauchy)
+    assert np.allclose(Heta, A @ eta, rtol=1e-9, atol=1e-12 * np.abs(Heta).max())
 
 
 def _solve_p2(g, k, seed=0):
