@@ -287,9 +287,14 @@ pspec_status pspec_solve_batched(pspec_graph* g, int k, const double* p_schedule
  * cluster is re-seeded at the row farthest from its centre; stop when no
  * label changes or after max_iter updates; the restart with the smallest
  * inertia is kept.  1 <= dim <= 16, 1 <= n_clusters <= 64, n >= n_clusters.
+ * The centres of FP32 rows are means of exact fixed-point sums at a scale
+ * 2^q set from max |x| and n (within 2^-q of the exact mean, plus one
+ * rounding); FP64 rows are summed in FP64.
  *   labels_out device int32[n]; centers_out device FP64[n_clusters*dim]
  *   (may be NULL); inertia_out host double (may be NULL).
- * Synchronises `stream`. */
+ * Synchronises `stream`.  Returns INVALID_ARG for bad sizes or NULL X or
+ * labels_out, and for FP32 rows holding a NaN or an infinity; CUDA or OOM
+ * on device errors. */
 pspec_status pspec_kmeans(const void* X, int64_t n, int dim, pspec_dtype dtype, int n_clusters,
                           uint64_t seed, int restarts, int max_iter, int32_t* labels_out,
                           double* centers_out, double* inertia_out, void* stream);
