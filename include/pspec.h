@@ -176,10 +176,14 @@ pspec_status pspec_tune(pspec_graph* g, const float* U, const float* V, int k, d
 /* ------------------------------------------------------ hvp, no allocation ---
  * pspec_hvp_noalloc: the same Hessian-vector product as pspec_hvp (FP32,
  * device pointers), for callers that must not allocate device memory: code
- * that runs where cudaMalloc is forbidden or unsafe (a host callback on a
- * stream, a section that must not synchronise the device, an allocator
- * owned by another runtime) or that cannot create a graph handle.  The paper
- * has no counterpart; this is an interface convenience.
+ * whose device memory belongs to another runtime's allocator (a framework's
+ * caching pool, an application that hands out fixed buffers), a section that
+ * must not enter cudaMalloc because it can synchronise the device, or code
+ * that cannot create a graph handle (creating one allocates).  The call
+ * enqueues a memset and kernels on `stream`, so, like any CUDA call, it must
+ * not be made from a host function running on a stream (cudaLaunchHostFunc,
+ * stream callbacks).  The paper has no counterpart; this is an interface
+ * convenience.
  *   rowptr/col/val: W in CSR (both triangles, FP32 weights), device memory
  *   U, V, HV_out:   n x k row-major FP32, device memory, HV_out not aliasing
  * Working memory (the rows of Delta_p u and the reduction partials) is one
@@ -190,14 +194,18 @@ pspec_status pspec_tune(pspec_graph* g, const float* U, const float* V, int k, d
  * The first call on a device, with that device current, looks up the
  * array's device address; make that first call before any stream capture.
  * Every call uses the same array: calls whose work overlaps on the GPU
- * (other streams, other host threads) race and give wrong results.  Errors:
- * INVALID_ARG, CUDA.  Enqueued on `stream`; does not synchronise. */
+ * (other streams, other host threads) race and give wrong results.  The
+ * looked-up address is kept for the life of the process: do not use the call
+ * across a cudaDeviceReset of that device.  There is no handle and hence no
+ * status word: a non-finite intermediate (NONFINITE for pspec_hvp) shows up
+ * as a NaN or an infinity in HV_out, and a zero column norm as infinities.
+ * Errors: INVALID_ARG, CUDA.  Enqueued on `stream`; does not synchronise. */
 pspec_status pspec_hvp_noalloc(int64_t n, const int64_t* rowptr, const int32_t* col,
                                const float* val, const float* U, const float* V, int k, double p,
                                float* HV_out, void* stream);
 
 /* ---------------------------------------------------------------- solve ---
- * pspec_solve: minimise Eq. 1 "for progressively smaller values of p"
+ * pspec_solve: minimise Eq. 1 while p is continued from 2 toward 1
  * (Section 2): for each p of p_schedule (each in (1,2], non-increasing), a
  * trust-region Newton method on Gr(k, n) whose subproblems are solved by
  * truncated CG; tangent projection P_U(G) = G - U U^T G, Riemannian Hessian

@@ -37,8 +37,19 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
+// a - b with a subnormal result flushed to zero, the same flush lg2.approx.ftz
+// applies to its argument: a difference is either zero (a tie) or has a
+// finite base-2 logarithm.
+__device__ __forceinline__ float sub_ftz(float a, float b) {
+  float y;
+  asm("sub.ftz.f32 %0, %1, %2;" : "=f"(y) : "f"(a), "f"(b));
+  return y;
+}
+
 // |x|^(p-2) for x != 0; for x == 0 the log is clamped so that the result is
 // finite (2^(126 (2-p))) and x * result == 0, which gives phi_p(0) = 0.
+// Only for terms without a weight: with a weight w the clamped value
+// w 2^(126 (2-p)) can overflow, and the edge kernels select on x == 0 instead.
 __device__ __forceinline__ float abs_pow_pm2_clamped(float x, float pm2) {
   float t = fmaxf(lg2_approx(fabsf(x)), -126.0f);
   return ex2_approx(pm2 * t);

@@ -9,11 +9,13 @@
 //           Delta_i                                              -> out_b
 //         and sigma_N = sum_i Delta_i v_i, sigma_D = sum_i phi_p(u_i) v_i.
 //
-// Arithmetic.  Every stored entry (i, j) costs one lg2 and one ex2 per column:
-// w_ij |d|^(p-2) = 2^((p-2) log2|d| + log2 w_ij), with log2 w_ij stored in
-// the graph's sorted copy (computed once, in double, at upload), then
-// phi = that * d and |d|^p = phi * d.  An exact zero difference gives phi = 0
-// (the log is clamped, see common.cuh) and, for p < 2, no curvature term.
+// Arithmetic.  Every stored entry (i, j) costs one lg2 and one ex2 per column,
+// with log2 w_ij stored in the graph's sorted copy (computed once, in double,
+// at upload): the objective forms w_ij phi_p(d) = sign(d) 2^((p-1) log2|d| +
+// log2 w_ij) and |d|^p w_ij = that * d; the Hessian product forms
+// w_ij |d|^(p-2) = 2^((p-2) log2|d| + log2 w_ij) and phi from it.  A zero
+// difference (a subnormal one flushed to zero) gives phi = 0 for any weight
+// and, for p < 2, no curvature term.
 //
 // Data movement.  The kernels read a copy of W whose rows are stably sorted
 // by degree (perm maps a sorted row back to its vertex), with each entry's
@@ -152,9 +154,17 @@ __device__ __forceinline__ bool task_is_hub(int4 t) { return ((t.z >> 8) & 1) !=
 
 // G entries of a lane's row: gather the neighbour rows, then accumulate
 //   dsum += w phi_p(d),  nsum += w |d|^p,  ssum += w |d|^(p-2) (v_i - v_j)
+// `ex` is the exponent of the power formed per entry: p - 1 for the
+// objective, p - 2 for the Hessian product.
+//  * objective: w phi_p(d) = sign(d) 2^((p-1) log2|d| + log2 w) directly; a tie
+//    (d == 0) has log2|d| = -inf and gives 0 for every weight.
+//  * Hessian product: w |d|^(p-2) = 2^((p-2) max(log2|d|, -126) + log2 w), then
+//    phi = that * d.  A tie is selected away before the product (p < 2: no
+//    curvature term; p = 2: the term is w), so a large weight never meets
+//    inf * 0.
 template <int K, int CPL, int VW, bool HVP, int G>
 __device__ __forceinline__ void edge_group(const EdgeArgs& a, const int2 (&e)[G], int c0,
-                                           const float (&ui)[CPL], const float (&vi)[CPL], float pm2,
+                                           const float (&ui)[CPL], const float (&vi)[CPL], float ex,
                                            bool zero_rule, float (&dsum)[CPL], float (&nsum)[CPL],
                                            float (&ssum)[CPL]) {
   float uj[G][CPL], vj[G][CPL];
@@ -168,14 +178,18 @@ __device__ __forceinline__ void edge_group(const EdgeArgs& a, const int2 (&e)[G]
     const float lw = __int_as_float(e[u].y);
 #pragma unroll
     for (int c = 0; c < CPL; ++c) {
-      const float d = ui[c] - uj[u][c];
-      const float sw = ex2_approx(fmaf(pm2, fmaxf(lg2_approx(fabsf(d)), -126.0f), lw));
-      const float ph = sw * d;  // w phi_p(d)
-      dsum[c] += ph;
-      nsum[c] = fmaf(ph, d, nsum[c]);  // w |d|^p
+      const float d = sub_ftz(ui[c], uj[u][c]);
       if constexpr (HVP) {
-        const float sz = (zero_rule && d == 0.0f) ? 0.0f : sw;
+        const float sw = ex2_approx(fmaf(ex, fmaxf(lg2_approx(fabsf(d)), -126.0f), lw));
+        const float sz = (zero_rule && d == 0.0f) ? 0.0f : sw;  // w |d|^(p-2)
+        const float ph = sz * d;                                 // w phi_p(d)
+        dsum[c] += ph;
+        nsum[c] = fmaf(ph, d, nsum[c]);
         ssum[c] = fmaf(sz, vi[c] - vj[u][c], ssum[c]);
+      } else {
+        const float ph = copysignf(ex2_approx(fmaf(ex, lg2_approx(fabsf(d)), lw)), d);  // w phi_p(d)
+        dsum[c] += ph;
+        nsum[c] = fmaf(ph, d, nsum[c]);  // w |d|^p
       }
     }
   }
@@ -213,6 +227,7 @@ __global__ void __launch_bounds__(kBlock, edge_min_blocks<K, HVP>()) edge_kernel
   const int gwarp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * kBlock) >> 5;
   const float pm2 = a.pm2;
+  const float ex = HVP ? pm2 : a.p - 1.0f;  // exponent of the per-entry power
   const bool zero_rule = pm2 != 0.0f;  // p < 2: a zero difference has no curvature
 
   Acc acc;
@@ -257,13 +272,13 @@ __global__ void __launch_bounds__(kBlock, edge_min_blocks<K, HVP>()) edge_kernel
 #pragma unroll
       for (int u = 0; u < UNR; ++u) e[u] = nx[u];
       if (j + 2 * UNR <= n_my) load_entries<UNR>(cw + (j + UNR) * E, E, nx);  // next step's entries
-      edge_group<K, CPL, VW, HVP, UNR>(a, e, c0, ui, vi, pm2, zero_rule, dsum, nsum, ssum);
+      edge_group<K, CPL, VW, HVP, UNR>(a, e, c0, ui, vi, ex, zero_rule, dsum, nsum, ssum);
     }
     if constexpr (UNR >= 4) {
       if (n_my - j >= 2) {
         int2 e[2];
         load_entries<2>(cw + j * E, E, e);
-        edge_group<K, CPL, VW, HVP, 2>(a, e, c0, ui, vi, pm2, zero_rule, dsum, nsum, ssum);
+        edge_group<K, CPL, VW, HVP, 2>(a, e, c0, ui, vi, ex, zero_rule, dsum, nsum, ssum);
         j += 2;
       }
     }
@@ -271,7 +286,7 @@ __global__ void __launch_bounds__(kBlock, edge_min_blocks<K, HVP>()) edge_kernel
       if (j < n_my) {  // at most one entry left
         int2 e[1];
         load_entries<1>(cw + j * E, E, e);
-        edge_group<K, CPL, VW, HVP, 1>(a, e, c0, ui, vi, pm2, zero_rule, dsum, nsum, ssum);
+        edge_group<K, CPL, VW, HVP, 1>(a, e, c0, ui, vi, ex, zero_rule, dsum, nsum, ssum);
       }
     }
     // row sums across the E edge slots of each team (lanes of equal q)

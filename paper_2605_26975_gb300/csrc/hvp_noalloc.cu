@@ -1,19 +1,25 @@
 // pspec_hvp_noalloc: the Hessian-vector product of pspec_hvp for callers that
-// cannot allocate device memory -- code running where cudaMalloc is not
-// allowed or not wanted (inside a host callback, under an allocator that
-// another runtime owns, or in a hard-real-time path that must not touch the
-// allocator at all).  It takes the CSR arrays and blocks directly (no graph
-// handle: creating one allocates) and keeps its working memory -- the rows of
-// Delta_p u and the partial sums of the grid reduction -- in one file-scope
-// __device__ array of fixed size, which every GPU that loads the library holds
-// until the process exits.
+// cannot allocate device memory -- code whose device memory is owned by
+// another runtime's allocator (a framework's caching pool, an embedding
+// application that hands out fixed buffers), or a latency-critical path that
+// must not enter cudaMalloc, which can synchronise the device.  It takes the
+// CSR arrays and blocks directly (no graph handle: creating one allocates)
+// and keeps its working memory -- the rows of Delta_p u and the partial sums
+// of the grid reduction -- in one file-scope __device__ array of fixed size,
+// which every GPU that loads the library holds until the process exits.  The
+// call enqueues kernels and a memset, so like any CUDA call it must not be
+// made from a host function running on a stream (cudaLaunchHostFunc).
 //
 // Set-up: the first call on a device, with that device current, looks up the
 // array's device address with cudaGetSymbolAddress (host code cannot use the
-// array's name as a device pointer).  That first call should come before any
-// stream capture.  Calls share the array: two calls whose work overlaps on the
-// GPU (different streams, or different host threads on one device) race and
-// corrupt each other's results; serialise them.
+// array's name as a device pointer) and keeps it for the life of the process;
+// that first call should come before any stream capture, and the function
+// must not be used across a cudaDeviceReset of that device in the same
+// process (the kept address would be stale).  Calls share the array: two
+// calls whose work overlaps on the GPU (different streams, or different host
+// threads on one device) race and corrupt each other's results; serialise
+// them.  There is no status word: a non-finite intermediate shows up as a NaN
+// or an infinity in HV_out.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -104,12 +110,15 @@ __global__ void __launch_bounds__(kBlock) na_hvp_edges(NaArgs a) {
         }
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
-          const float d = ui[c] - uj[c];
+          // w |d|^(p-2); a tie (d == 0, subnormal differences flushed) has no
+          // curvature term for p < 2 and is selected away before phi = that * d,
+          // so a large weight never meets inf * 0
+          const float d = sub_ftz(ui[c], uj[c]);
           const float sw = ex2_approx(fmaf(a.pm2, fmaxf(lg2_approx(fabsf(d)), -126.0f), lw));
-          const float ph = sw * d;
+          const float sz = (zero_rule && d == 0.0f) ? 0.0f : sw;
+          const float ph = sz * d;
           ds[c] += ph;
           ns[c] = fmaf(ph, d, ns[c]);
-          const float sz = (zero_rule && d == 0.0f) ? 0.0f : sw;
           ss[c] = fmaf(sz, vi[c] - vj[c], ss[c]);
         }
       }

@@ -77,9 +77,41 @@ def grad_term_scale(oracle, g, U, p):
     return out
 
 
+def rel_elem(a, ref, scale):
+    """max over entries of |a - ref| / scale, with `scale` the magnitude of the
+    terms that make up ref (an entry whose scale is 0 must match exactly)."""
+    a = np.asarray(a, dtype=np.float64).reshape(ref.shape)
+    err = np.abs(a - ref)
+    zero = scale == 0
+    if np.any(err[zero] != 0):
+        return float("inf")
+    return float(np.max(np.where(zero, 0.0, err / np.where(zero, 1.0, scale)), initial=0.0))
+
+
+def tied_heavy_graph(seed=12, n=3000):
+    """SBM with weights log-uniform in [1, 1e6]: with quantised blocks many
+    entries tie (u_i == u_j) under a weight far above 2^(128 - 126 (2 - p)),
+    the size at which w 2^(126 (2 - p)) leaves the FP32 range for p near 1."""
+    rng = np.random.default_rng(seed)
+    g = wl.sbm_sampled(rng, n, 4, 12.0, 0.85)
+    rows = np.repeat(np.arange(n), np.diff(g.rowptr))
+    keep = rows < g.col
+    a, b = rows[keep], g.col[keep].astype(np.int64)
+    w = 10.0 ** rng.uniform(0.0, 6.0, a.size)
+    return wl.csr_from_undirected(n, a, b, w)
+
+
+def quantised_block(seed, n, k):
+    """Values in {-0.75, -0.5, ..., 0.75}: many exact ties and exact zeros."""
+    rng = np.random.default_rng(seed)
+    return (rng.integers(-3, 4, size=(n, k)) * 0.25).astype(np.float32)
+
+
 def hvp_term_scale(oracle, g, U, V, p):
     """Magnitudes of the terms of the exact Hessian product: the sparse part,
-    the diagonal part and the three rank-two terms, added term by term."""
+    the diagonal part and the three rank-two terms, added term by term (the
+    column dots <g_D, v>, <g_N, v> as sums of the magnitudes of their terms,
+    which is what bounds their rounding)."""
     rows, col, w = oracle.edge_list(g)
     N, D = oracle.objective_parts(g, U, p)
     c = p * (p - 1.0)
@@ -92,7 +124,7 @@ def hvp_term_scale(oracle, g, U, V, p):
         diag = lam * c * oracle.abs_pow_pm2(u, p) * np.abs(v)
         gN = p * oracle.p_laplacian(g, U[:, l:l + 1], p)[:, 0]
         gD = p * oracle.phi_p(u, p)
-        r2 = (np.abs(gN) * abs(gD @ v) + np.abs(gD) * abs(gN @ v)
-              + 2 * lam * np.abs(gD) * abs(gD @ v)) / D[l] ** 2
+        aDv, aNv = np.abs(gD) @ np.abs(v), np.abs(gN) @ np.abs(v)
+        r2 = (np.abs(gN) * aDv + np.abs(gD) * aNv + 2 * lam * np.abs(gD) * aDv) / D[l] ** 2
         out[:, l] = (s + diag) / D[l] + r2
     return out

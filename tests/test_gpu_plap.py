@@ -7,7 +7,8 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_common import TOL_F, TOL_F64, TOL_GRAD, TOL_HVP, rel_col, small_graphs
+from gpu_common import (TOL_F, TOL_F64, TOL_GRAD, TOL_HVP, grad_term_scale, hvp_term_scale,
+                        quantised_block, rel_col, rel_elem, small_graphs, tied_heavy_graph)
 from paper_2605_26975_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -52,7 +53,11 @@ def check_eval(api, g, G, U, p):
     k = U.shape[1]
     assert np.allclose(P[:k], N, rtol=TOL_F, atol=0)
     assert np.allclose(P[k:], D, rtol=TOL_F, atol=0)
-    assert rel_col(grad.cpu().numpy(), gr_ref) <= TOL_GRAD
+    got = grad.cpu().numpy()
+    assert rel_col(got, gr_ref) <= TOL_GRAD
+    # entry by entry, against the magnitude of the entry's terms: a wrong
+    # value on a low-degree or small-|u| row cannot hide in a column norm
+    assert rel_elem(got, gr_ref, grad_term_scale(oracle, g, U64, p)) <= TOL_GRAD
 
 
 def check_hvp(api, g, G, U, V, p):
@@ -61,8 +66,11 @@ def check_hvp(api, g, G, U, V, p):
     HV = G.hvp(Ud, Vd, p)
     torch.cuda.synchronize()
     assert G.status() == 0
-    ref = oracle.euclidean_hvp(g, U.astype(np.float64), V.astype(np.float64), p)
-    assert rel_col(HV.cpu().numpy(), ref) <= TOL_HVP
+    U64, V64 = U.astype(np.float64), V.astype(np.float64)
+    ref = oracle.euclidean_hvp(g, U64, V64, p)
+    got = HV.cpu().numpy()
+    assert rel_col(got, ref) <= TOL_HVP
+    assert rel_elem(got, ref, hvp_term_scale(oracle, g, U64, V64, p)) <= TOL_HVP
 
 
 @pytest.mark.parametrize("name", ["sbm", "grid", "knn", "hubs", "isolated"])
@@ -90,6 +98,26 @@ def test_ties_and_zeros(api, graphs, p):
     rng = np.random.default_rng(9)
     U = (rng.integers(-3, 4, size=(g.n, 4)) * 0.25).astype(np.float32)
     V = rng.standard_normal((g.n, 4)).astype(np.float32)
+    check_eval(api, g, G, U, p)
+    check_hvp(api, g, G, U, V, p)
+
+
+@pytest.fixture(scope="module")
+def tied_heavy(api):
+    g = tied_heavy_graph()
+    return g, api.Graph.from_csr(g)
+
+
+@pytest.mark.parametrize("p", [1.01, 1.05, 1.1, 2.0])
+@pytest.mark.parametrize("k", [4, 8, 3])
+def test_ties_with_large_weights(api, tied_heavy, p, k):
+    """Tied entries (u_i == u_j) under weights up to 1e6: a tie contributes
+    phi_p(0) = 0 and, for p < 2, no curvature term, whatever its weight, so
+    every result is finite and equals the oracle's (no status raised)."""
+    g, G = tied_heavy
+    assert g.val.max() > 2.0 ** (128 - 126 * (2 - 1.01))  # beyond FP32 when clamped
+    U = quantised_block(40 + k, g.n, k)
+    V = wl.gaussian_block(41 + k, g.n, k, dtype=np.float32)
     check_eval(api, g, G, U, p)
     check_hvp(api, g, G, U, V, p)
 

@@ -30,6 +30,49 @@ def test_splitmix64_reference_outputs():
     assert min(vals) >= 0.0 and max(vals) < 1.0
 
 
+def test_kmeans_pp_hand_example():
+    """k-means++ seeding on the five points 0, 1, 3, 7, 15 with SplitMix64(0),
+    worked by hand from the golden outputs of that stream:
+      u0 = 16294208416658607535 / 2^64 = 0.88331...  -> first centre row
+           floor(5 u0) = 4 (x = 15); D^2 = 225, 196, 144, 64, 0 (sum 629)
+      u1 = 7960286522194355700 / 2^64 = 0.43153...   -> u1 * 629 = 271.43, first
+           running sum of D^2 above it is 421 at row 1 (x = 1);
+           D^2 = min(previous, distance to 1) = 1, 0, 4, 36, 0 (sum 41)
+      u2 = 487617019471545679 / 2^64 = 0.02643...    -> u2 * 41 = 1.084, first
+           running sum above it is 5 at row 2 (x = 3).
+    Weighting by D instead of D^2 picks row 0 third; not lowering D^2 to the
+    nearest chosen centre picks row 3."""
+    X = np.array([[0.0], [1.0], [3.0], [7.0], [15.0]])
+    centres = oracle.kmeans_pp(X, 3, oracle.SplitMix64(0))
+    assert centres[:, 0].tolist() == [15.0, 1.0, 3.0]
+
+
+def test_kmeans_pp_draw_follows_d_squared():
+    """Over many seeds the second centre, given the first, is drawn with
+    probability D^2 / sum D^2 (chi-square goodness of fit, 20,000 draws)."""
+    from scipy import stats
+    X = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 2.0], [3.0, 1.0], [-2.0, -1.0]])
+    n = X.shape[0]
+    counts = np.zeros((n, n))
+    for seed in range(20_000):
+        c = oracle.kmeans_pp(X, 2, oracle.SplitMix64(seed))
+        f = int(np.flatnonzero((X == c[0]).all(1))[0])
+        s = int(np.flatnonzero((X == c[1]).all(1))[0])
+        counts[f, s] += 1
+    chi2, dof = 0.0, 0
+    for f in range(n):
+        d2 = ((X - X[f]) ** 2).sum(1)
+        expected = counts[f].sum() * d2 / d2.sum()
+        assert counts[f, f] == 0  # a chosen point has D^2 = 0
+        m = expected > 0
+        chi2 += float((((counts[f] - expected) ** 2)[m] / expected[m]).sum())
+        dof += int(m.sum()) - 1
+    assert stats.chi2.sf(chi2, dof) > 1e-3, (chi2, dof)
+    # the first centre is uniform over the rows
+    first = counts.sum(1)
+    assert stats.chisquare(first).pvalue > 1e-3
+
+
 def _inertia(X, labels, C):
     tot = 0.0
     for c in range(C):

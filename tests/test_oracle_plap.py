@@ -284,12 +284,57 @@ def test_alg1_plus_rank_two_is_exact_hessian(p):
 def test_zero_difference_reading(p):
     # equal neighbouring values: that edge contributes no curvature (reading
     # for |d|^(p-2) at d == 0); a vertex value of 0 contributes no vertex term
+    # Path 0 -(w=1)- 1 -(w=2)- 2 with u = (1/2, 1/2, -1): the edge 0-1 ties.
+    # Worked by hand: N = 2 (3/2)^p, D = 2 (1/2)^p + 1, lambda = N / D,
+    # g_N = p Delta_p u = (0, 2p (3/2)^(p-1), -2p (3/2)^(p-1)),
+    # g_D = p phi_p(u) = (p h, p h, -p) with h = (1/2)^(p-1).
     g = dense_graph(np.array([[0, 1.0, 0], [1.0, 0, 2.0], [0, 2.0, 0]]))
     U = np.array([[0.5], [0.5], [-1.0]])
-    V = np.array([[1.0], [0.0], [0.0]])
-    H = oracle.euclidean_hvp(g, U, V, p)
-    assert np.all(np.isfinite(H))
+    c = p * (p - 1.0)
+    N, D = 2 * 1.5 ** p, 2 * 0.5 ** p + 1
+    lam = N / D
+    h, t = 0.5 ** (p - 1), 1.5 ** (p - 1)
+    gN = np.array([0.0, 2 * p * t, -2 * p * t])
+    gD = np.array([p * h, p * h, -p])
+
+    def expect(HNv, HDv, v):
+        cN, cD = gN @ v, gD @ v
+        return (HNv - lam * HDv) / D - (gN * cD + gD * cN - 2 * lam * gD * cD) / D ** 2
+
+    # v = e_0: vertex 0's only edge ties, so the sparse part is 0 everywhere
+    # (a clamped or regularised |0|^(p-2) would make it huge); the vertex term
+    # is p(p-1) (1/2)^(p-2) at vertex 0.
+    v = np.array([1.0, 0.0, 0.0])
+    ref = expect(np.zeros(3), np.array([c * 0.5 ** (p - 2), 0, 0]), v)
+    # the same entries expanded by hand
+    assert np.allclose(ref, [-lam * c * 0.5 ** (p - 2) / D + 2 * lam * p * p * h * h / D ** 2,
+                             -(2 * p * p * t * h - 2 * lam * p * p * h * h) / D ** 2,
+                             (2 * p * p * t * h - 2 * lam * p * p * h) / D ** 2], rtol=1e-14)
+    H = oracle.euclidean_hvp(g, U, v[:, None], p)[:, 0]
+    assert np.allclose(H, ref, rtol=1e-13, atol=0)
+    # v = e_1: only the untied edge 1-2 bends, 2 (3/2)^(p-2) (v_1 - v_2) at 1
+    # and at 2 the mirror; the tie 0-1 adds nothing at 0 or 1
+    v = np.array([0.0, 1.0, 0.0])
+    s = 2 * 1.5 ** (p - 2)
+    ref = expect(c * np.array([0.0, s, -s]), np.array([0, c * 0.5 ** (p - 2), 0]), v)
+    H = oracle.euclidean_hvp(g, U, v[:, None], p)[:, 0]
+    assert np.allclose(H, ref, rtol=1e-13, atol=0)
+    # a zero vertex value: u = (0, 1/2, -1), v = e_0 gives no vertex term at 0
+    # and phi_p(0) = 0 in g_D
+    U0 = np.array([[0.0], [0.5], [-1.0]])
     assert oracle.abs_pow_pm2(np.array([0.0, 2.0]), p)[0] == 0.0
+    assert oracle.phi_p(0.0, p) == 0.0
+    H0 = oracle.euclidean_hvp(g, U0, np.array([[1.0], [0.0], [0.0]]), p)
+    assert np.all(np.isfinite(H0))
+    N0 = 0.5 ** p + 2 * 1.5 ** p
+    D0 = 0.5 ** p + 1
+    lam0 = N0 / D0
+    gN0 = p * np.array([-(0.5 ** (p - 1)), 0.5 ** (p - 1) + 2 * t, -2 * t])
+    gD0 = p * np.array([0.0, h, -1.0])
+    HN0 = c * np.array([0.5 ** (p - 2), -(0.5 ** (p - 2)), 0.0])  # edge 0-1: |d| = 1/2
+    cN0, cD0 = gN0[0], gD0[0]
+    ref0 = (HN0 - lam0 * 0.0) / D0 - (gN0 * cD0 + gD0 * cN0 - 2 * lam0 * gD0 * cD0) / D0 ** 2
+    assert np.allclose(H0[:, 0], ref0, rtol=1e-13, atol=1e-15)
 
 
 def test_p2_hessian_with_ties_is_laplacian():
