@@ -1,20 +1,23 @@
 """Benchmark of the p-spectral clustering hot path on GB300.
 
-One step = one pspec_eval (objective + gradient) and one pspec_hvp
-(Hessian-vector product) on the workload's graph: 2 * nnz * k edge-columns.
-The metric is edge-columns per second over the whole job (all ranks), with
-inputs resident in HBM and the L2 flushed (a 256 MB write) before every timed
-step.  Alongside:
+One step = one pspec_eval (objective + gradient, keeping Delta_p u) and one
+pspec_hvp (Hessian-vector product at the same U, reusing Delta_p u) on the
+workload's graph -- the pattern of a Newton step, which evaluates once at U
+and applies the Hessian at U: 2 * nnz * k edge-columns.  The metric is
+edge-columns per second over the whole job (all ranks), with inputs resident
+in HBM and the L2 flushed (a 256 MB write) before every timed step.
+Alongside:
   roofline      the dominant kernel's algorithmic bytes per launch over its
                 mean CUDA-event duration, against the measured HBM copy peak
   e2e           the same metric through the C ABI with host (pinned) buffers,
                 host<->device copies inside the timed region
-  cpu_baseline  the FP64 oracle on the host cores, on a bounded sample
-  solve         wall time of the full solve down to the schedule's last p,
-                FP32 path vs the plain FP64 path, with their RCut
+  cpu_baseline  the FP64 C oracle on every host core (OpenMP), full steps of
+                the workload, plus a single-thread sample
+  solve         wall time of the full solve down to the schedule's last p
+                (FP32; with --solve both also the plain FP64 path), with RCut
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload knn_gmm]
-                    [--impl ours|reference] [--no-solve]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload grid3d]
+                    [--impl ours|reference] [--solve none|f32|both]
 Multi-GPU (torchrun): every rank runs an independent replica (its own seed);
 there is no data-path collective (weak scaling).
 """
@@ -40,10 +43,12 @@ from paper_2605_26975_gb300 import workloads as wl  # noqa: E402
 P_BENCH = 1.3
 METRIC = "p-Lap grad+HVP edge·col/s & % HBM peak; solve time to p=1.1 vs FP64 plain"
 UNIT = "edge*col/s"
-STEP = "pspec_eval (F + grad) + pspec_hvp"
+STEP = "pspec_eval (F + grad, Delta_p u kept) + pspec_hvp at the same U (Delta_p u reused)"
+STEP_PLAIN = "pspec_eval (F + grad) + pspec_hvp"
 L2_NOTE = "flushed (256 MB write) before every timed step"
 L2_FLUSH_BYTES = 256 << 20
 KERNEL_SOURCES = ["paper_2605_26975_gb300/csrc/edge_kernels.cuh",
+                  "paper_2605_26975_gb300/csrc/edge_staged.cuh",
                   "paper_2605_26975_gb300/csrc/edge_launch.cuh",
                   "paper_2605_26975_gb300/csrc/common.cuh"]
 
@@ -54,10 +59,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=None,
                     help="timed steps (default: enough for about 2 s of timed region, at least 50)")
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="knn_gmm",
+    ap.add_argument("--workload", default="grid3d",
                     choices=["knn_gmm", "grid3d", "dcsbm", "sbm4", "sbm_batch"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--solve", default="f32", choices=["none", "f32", "both"],
+                    help="full solve to the schedule's last p: FP32 only, or FP32 and plain FP64")
+    ap.add_argument("--solve-gtol", type=float, default=None,
+                    help="relative gradient tolerance of every stage (library default 1e-6)")
+    ap.add_argument("--no-solve", action="store_true", help="same as --solve none")
+    ap.add_argument("--no-keep", action="store_true",
+                    help="plain pspec_hvp (the HVP kernel writes Delta_p u again)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--eager", action="store_true", help="launch the step's kernels one by one")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape (no pspec_tune)")
@@ -113,12 +124,27 @@ def build_parts(name, rank=0):
     return [Part(g, None, None, U, V, info["k"])], info
 
 
+def q_of(k):
+    """Column lanes per row of the edge kernels for k columns (as the library)."""
+    return 4 if (k % 4 == 0 and k // 4 >= 4) else 2 if (k % 2 == 0 and k // 2 >= 4) else 1
+
+
+def staged_max_entries(k):
+    """Most entries per warp task the staged edge kernel takes for k columns."""
+    return min(256, 8192 // (8 * k))
+
+
 def bytes_eval_edges(g, k):
+    """Algorithmic bytes of the objective's edge kernel: the matrix (column
+    index + weight per entry), the row offsets, U in and Delta_p u out."""
     return g.nnz * 8 + (g.n + 1) * 8 + 2 * g.n * k * 4
 
 
 def bytes_hvp_edges(g, k):
-    return g.nnz * 8 + (g.n + 1) * 8 + 4 * g.n * k * 4
+    """Algorithmic bytes of the Hessian product's edge kernel: the matrix, the
+    row offsets, U and V in, the sparse part out (Delta_p u is the
+    objective's, kept from the evaluation at the same U)."""
+    return g.nnz * 8 + (g.n + 1) * 8 + 3 * g.n * k * 4
 
 
 def source_hash():
@@ -280,20 +306,31 @@ def build_workload(name, seed_shift=0):
     return g, U, V, info
 
 
-def oracle_steps(parts, p, budget_s, max_steps):
-    """The oracle as it stands (numpy FP64, one thread): eval+grad+HVP on the
-    workload's graphs in order (cycling) until budget_s seconds or max_steps
-    graph-steps pass.  Returns (edge-columns done, seconds, graph-steps)."""
-    import oracle
-    items = [(g, U.astype(np.float64), V.astype(np.float64), part.k)
-             for part in parts for g, U, V in part.samples()]
+def oracle_items(parts):
+    """(graph, CSR as the C oracle takes it, U, V in FP64, k) of every graph of
+    the workload."""
+    items = []
+    for part in parts:
+        for g, U, V in part.samples():
+            csr = (np.ascontiguousarray(g.rowptr, dtype=np.int64),
+                   np.ascontiguousarray(g.col, dtype=np.int32),
+                   np.ascontiguousarray(g.val, dtype=np.float64))
+            items.append((g, csr, U.astype(np.float64), V.astype(np.float64), part.k))
+    return items
+
+
+def oracle_steps(items, p, budget_s, max_steps):
+    """The FP64 C oracle as it stands: objective + gradient and the Hessian
+    product on the workload's graphs in order (cycling) until budget_s
+    seconds or max_steps graph-steps pass.  Returns (edge-columns done,
+    seconds, graph-steps)."""
+    from oracle import omp
     t0 = time.perf_counter()
     done = steps = 0
     while True:
-        g, U64, V64, k = items[steps % len(items)]
-        oracle.objective(g, U64, p)
-        oracle.euclidean_grad(g, U64, p)
-        oracle.euclidean_hvp(g, U64, V64, p)
+        g, csr, U64, V64, k = items[steps % len(items)]
+        omp.evaluate(g, U64, p, csr=csr)
+        omp.hvp(g, U64, V64, p, csr=csr)
         done += 2 * g.nnz * k
         steps += 1
         if time.perf_counter() - t0 > budget_s or steps >= max_steps:
@@ -301,38 +338,80 @@ def oracle_steps(parts, p, budget_s, max_steps):
     return done, time.perf_counter() - t0, steps
 
 
-def cpu_baseline(parts, p, budget_s=12.0):
-    """The oracle on a bounded sample of the workload (~budget_s seconds)."""
-    max_steps = 20 if len(parts) == 1 else 10_000
-    done, dt, steps = oracle_steps(parts, p, budget_s, max_steps)
-    what = "full eval+grad+HVP step(s)" if len(parts) == 1 else "graphs' eval+grad+HVP steps"
-    return {"value": done / dt, "unit": "edge*col/s", "cores": 1, "kind": "oracle",
-            "sample": f"{steps} {what} of the FP64 numpy oracle on this workload "
-                      f"({dt:.1f} s, single-threaded numpy)"}
+class RowBlock:
+    """The first `rows` rows of a graph (all columns kept): a bounded sample of
+    its work for the single-thread oracle."""
+
+    def __init__(self, g, rows):
+        self.n = rows
+        self.nnz = int(g.rowptr[rows])
+
+
+def single_thread_sample(items, p, edge_cols=4_000_000):
+    """The C oracle on one thread, one objective + gradient + Hessian product
+    over a row block of the first graph with about edge_cols edge-columns."""
+    from oracle import omp
+    g, csr, U64, V64, k = items[0]
+    rows = int(np.searchsorted(csr[0], edge_cols // (2 * k), side="right")) - 1
+    rows = max(1, min(g.n, rows))
+    blk = RowBlock(g, rows)
+    sub = (csr[0][:rows + 1], csr[1][:blk.nnz], csr[2][:blk.nnz])
+    omp.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        omp.evaluate(blk, U64, p, csr=sub)
+        omp.hvp(blk, U64, V64, p, csr=sub)
+        dt = time.perf_counter() - t0
+    finally:
+        omp.set_threads(os.cpu_count() or 1)
+    return {"value": 2 * blk.nnz * k / dt, "cores": 1,
+            "sample": f"one eval+grad+HVP of rows 0..{rows} ({blk.nnz} entries, k={k}) "
+                      f"of the first graph, {dt:.2f} s"}
+
+
+def cpu_baseline(parts, p, budget_s=15.0):
+    """The FP64 C oracle on every host core (OpenMP over rows), full steps of
+    the workload for about budget_s seconds, plus a single-thread sample."""
+    from oracle import omp
+    items = oracle_items(parts)
+    cores = omp.set_threads(os.cpu_count() or 1)
+    oracle_steps(items[:1], p, 0.0, 1) if items[0][0].nnz < 50_000_000 else None  # warm-up
+    max_steps = 20 if len(items) == 1 else 100_000
+    done, dt, steps = oracle_steps(items, p, budget_s, max_steps)
+    what = "full eval+grad+HVP step(s)" if len(items) == 1 else "graphs' eval+grad+HVP steps"
+    return {"value": done / dt, "unit": "edge*col/s", "cores": cores, "kind": "oracle",
+            "sample": f"{steps} {what} of the FP64 C oracle (OpenMP, {cores} threads) on this "
+                      f"workload, {dt:.1f} s",
+            "single_thread": single_thread_sample(items, p)}
 
 
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
+    from oracle import omp
     parts, info = build_parts(args.workload)
+    items = oracle_items(parts)
+    cores = omp.set_threads(os.cpu_count() or 1)
     # each timed step is one oracle eval+grad+HVP of the workload's graph (of
     # up to 40 of a batch's graphs); keep the run to a few minutes
-    steps = max(1, min(args.steps, 5))
-    per_step = 1 if len(parts) == 1 else 40
-    oracle_steps(parts, P_BENCH, 0.0, 1)  # warm-up
-    done, dt, _ = oracle_steps(parts, P_BENCH, float("inf"), steps * per_step)
+    steps = max(1, min(args.steps or 5, 8))
+    per_step = 1 if len(items) == 1 else 40
+    oracle_steps(items, P_BENCH, 0.0, 1)  # warm-up
+    done, dt, _ = oracle_steps(items, P_BENCH, float("inf"), steps * per_step)
     value = done / dt
     line = {"impl": "reference", "metric": METRIC,
             "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": steps,
             "warmup": 1, "ms_per_step": 1e3 * dt / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": workload_desc(args.workload, parts),
-                                            "p": P_BENCH, "step": STEP,
+                                            "p": P_BENCH,
+                                            "step": "objective + gradient, then the Hessian "
+                                                    "product at the same U (FP64 C oracle)",
                                             "l2": "n/a (FP64 oracle on the host cores)",
                                             "parallelism": f"replicas x{args.gpus}"},
-            "cpu_baseline": {"value": value, "unit": "edge*col/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "edge*col/s", "cores": cores, "kind": "oracle",
                              "sample": f"{steps} step(s) of {per_step} graph eval+grad+HVP of the "
-                                       f"FP64 numpy oracle"},
+                                       f"FP64 C oracle (OpenMP, {cores} threads)"},
             "e2e": {"value": value, "unit": "edge*col/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -363,10 +442,13 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
+    # a batched handle keeps no Delta_p u: its step is the plain pair
+    keep = not args.no_keep and all(pt.G.n_graphs == 1 for pt in parts)
+
     def step():
         for pt in parts:
-            pt.G.eval(pt.Ud, P_BENCH, grad_out=pt.grad)
-            pt.G.hvp(pt.Ud, pt.Vd, P_BENCH, out=pt.HV)
+            pt.G.eval(pt.Ud, P_BENCH, grad_out=pt.grad, keep_delta=keep)
+            pt.G.hvp(pt.Ud, pt.Vd, P_BENCH, out=pt.HV, delta_kept=keep)
 
     # launch shape per handle from the autotuner (edges per lane, blocks per SM)
     tuned = []
@@ -375,7 +457,9 @@ def main():
             cands, best = pt.G.tune(pt.Ud, pt.Vd, P_BENCH, reps=3)
             L, b, ms = cands[best]
             tuned.append({"k": pt.k, "edges_per_lane": L, "blocks_per_sm": b,
-                          "eval_hvp_ms": round(ms, 4), "candidates": len(cands)})
+                          "kernel": "staged" if 32 * L // q_of(pt.k) <= staged_max_entries(pt.k) else "direct",
+                          "eval_hvp_ms": round(ms, 4),
+                          "candidates": [[c[0], c[1], round(c[2], 4)] for c in cands]})
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
@@ -488,8 +572,8 @@ def main():
 
     def host_step():
         for pt in parts:
-            pt.G.eval_host(pt.Uh, P_BENCH, pt.gh)
-            pt.G.hvp_host(pt.Uh, pt.Vh, P_BENCH, pt.hh)
+            pt.G.eval_host(pt.Uh, P_BENCH, pt.gh, keep_delta=keep)
+            pt.G.hvp_host(pt.Uh, pt.Vh, P_BENCH, pt.hh, delta_kept=keep)
 
     for _ in range(2):
         host_step()
@@ -507,26 +591,40 @@ def main():
            "h2d_bytes_per_step": 3 * blk, "d2h_bytes_per_step": 2 * blk + 8 * n_f,
            "note": "wall clock per step incl. a 256 MB L2 flush; copies and kernels synchronous"}
 
-    # ---- full solve to the last p, FP32 fast path vs plain FP64 path
+    # ---- full solve to the last p (FP32; with --solve both the plain FP64 path too)
     solve = None
-    if not args.no_solve and rank == 0 and len(parts) == 1:
+    if args.no_solve:
+        args.solve = "none"
+    if args.solve != "none" and rank == 0 and len(parts) == 1:
         pt = parts[0]
         sched = list(info["p_schedule"])
-        opts = api.default_opts()
-        t0 = time.perf_counter()
-        _, lab32, rc32, st32, s32 = pt.G.solve(pt.Ud, sched, opts)
-        t32 = time.perf_counter() - t0
-        U64 = torch.from_numpy(pt.U.astype(np.float64)).cuda()
-        t0 = time.perf_counter()
-        _, lab64, rc64, st64, s64 = pt.G.solve(U64, sched, opts)
-        t64 = time.perf_counter() - t0
-        solve = {"p_schedule": sched, "fast_f32_s": t32, "plain_f64_s": t64,
-                 "speedup": t64 / t32, "rcut_f32": rc32, "rcut_f64": rc64,
-                 "rcut_rel_diff": abs(rc32 - rc64) / rc64,
-                 "hvp_calls_f32": st32["hvp_calls"], "hvp_calls_f64": st64["hvp_calls"],
-                 "newton_steps_f32": sum(st32["outer"]), "newton_steps_f64": sum(st64["outer"])}
+        opts = api.default_opts() if args.solve_gtol is None else api.default_opts(gtol_rel=args.solve_gtol)
+        cap = opts.max_outer
 
-    if not args.no_solve and rank == 0 and len(parts) > 1:
+        def run_solve(U0):
+            t0 = time.perf_counter()
+            _, lab, rc, st, status = pt.G.solve(U0, sched, opts)
+            dt = time.perf_counter() - t0
+            return {"s": dt, "rcut": rc, "hvp_calls": st["hvp_calls"],
+                    "newton_steps": sum(st["outer"]), "stages_at_cap": sum(o >= cap for o in st["outer"]),
+                    "f": st["f"], "status": status}
+
+        solve = {"p_schedule": sched, "gtol_rel": opts.gtol_rel, "max_outer": cap,
+                 "f32": run_solve(pt.Ud)}
+        if args.solve == "both":
+            solve["f64"] = run_solve(torch.from_numpy(pt.U.astype(np.float64)).cuda())
+            solve["speedup"] = solve["f64"]["s"] / solve["f32"]["s"]
+            solve["rcut_rel_diff"] = abs(solve["f32"]["rcut"] - solve["f64"]["rcut"]) / solve["f64"]["rcut"]
+            # the same FP64 solve from U0 perturbed at FP32's rounding level
+            # (each entry times 1 + 2^-24 s, s = +-1 seeded): how far apart two
+            # FP64 paths end from starting points as close as FP32 rounding
+            sgn = np.where(np.random.default_rng(7).random(pt.U.shape) < 0.5, -1.0, 1.0)
+            U0p = pt.U.astype(np.float64) * (1.0 + 2.0 ** -24 * sgn)
+            solve["f64_perturbed"] = run_solve(torch.from_numpy(U0p).cuda())
+            solve["rcut_rel_diff_f64_perturbed"] = (abs(solve["f64_perturbed"]["rcut"] - solve["f64"]["rcut"])
+                                                    / solve["f64"]["rcut"])
+
+    if args.solve != "none" and rank == 0 and len(parts) > 1:
         # the batch: every graph solved on its own (pspec_solve_batched, FP32)
         sched = list(info["p_schedule"])
         t0 = time.perf_counter()
@@ -559,7 +657,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": workload_desc(args.workload, parts), "p": P_BENCH,
-                       "step": STEP + (" per handle" if len(parts) > 1 else "")
+                       "step": (STEP if keep else STEP_PLAIN) + (" per handle" if len(parts) > 1 else "")
                                + ("" if args.eager else ", replayed as a CUDA graph"),
                        "l2": L2_NOTE,
                        "launch_shape": tuned if tuned else "default (not tuned)",

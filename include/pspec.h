@@ -70,6 +70,8 @@ typedef enum { PSPEC_F32 = 0, PSPEC_F64 = 1 } pspec_dtype;
 #define PSPEC_HOST_PTRS 0x1u      /* pointer arguments are host memory         */
 #define PSPEC_CHECK_SYMMETRY 0x2u /* graph_create: verify w_ij == w_ji (host)  */
 #define PSPEC_HVP_ALG1 0x4u       /* hvp: Algorithm 1's form (see pspec_hvp)   */
+#define PSPEC_KEEP_DELTA 0x8u     /* eval: keep Delta_p u on the handle        */
+#define PSPEC_DELTA_KEPT 0x10u    /* hvp: reuse the kept Delta_p u (same U)    */
 
 typedef struct pspec_graph pspec_graph;
 
@@ -122,8 +124,15 @@ pspec_status pspec_graph_status(pspec_graph* g, void* stream);
  * graph every graph has k columns (group graphs of different k into
  * separate handles), F_out holds G values and parts_out G x 2k (graph g's
  * N then D at [g*2k]); the call runs the FP32 path only (dtype F32, else
- * INVALID_ARG).  Errors: INVALID_ARG (k, p, NULL, misalignment), CUDA;
- * ZERO_COLUMN and NONFINITE through the status word. */
+ * INVALID_ARG).
+ * With PSPEC_KEEP_DELTA in flags (FP32, single graph) the handle keeps the
+ * rows Delta_p u of this call (n x k FP32 in its workspace) together with
+ * the U pointer, k and p, for later pspec_hvp calls with PSPEC_DELTA_KEPT at
+ * the same point: the Newton step of Section 2 evaluates the gradient once at
+ * U and then applies the Hessian at U many times (truncated CG), and Delta_p u
+ * depends on U alone.  A later KEEP call replaces what is kept.
+ * Errors: INVALID_ARG (k, p, NULL, misalignment, KEEP on a batched graph or
+ * with FP64), CUDA; ZERO_COLUMN and NONFINITE through the status word. */
 pspec_status pspec_eval(pspec_graph* g, const void* U, int k, double p, pspec_dtype dtype,
                         double* F_out, void* grad_out, double* parts_out, unsigned flags,
                         void* stream);
@@ -142,7 +151,16 @@ pspec_status pspec_eval(pspec_graph* g, const void* U, int k, double p, pspec_dt
  * only, as pspec_eval).  With PSPEC_HVP_ALG1 in flags the rank-two terms
  * are left out: HV = (Hess N V - lambda Hess D V)/D per column, the sparse
  * (W's pattern) plus diagonal matrix that Algorithm 1 applies.  HV_out may
- * not alias U or V.  Errors as pspec_eval. */
+ * not alias U or V.
+ * With PSPEC_DELTA_KEPT in flags (FP32, single graph) the call takes the rows
+ * Delta_p u (needed by the rank-two terms) from the last pspec_eval with
+ * PSPEC_KEEP_DELTA instead of writing them again: one n x k block less of
+ * memory traffic per call.  That eval must have had the same U pointer
+ * (host or device, as passed), k and p, else INVALID_ARG; the caller
+ * guarantees that U's contents have not changed since, and orders both calls
+ * on one stream.  The result equals the plain call's within rounding (the
+ * objective's and the Hessian's kernels form phi_p by different power
+ * formulas).  Errors as pspec_eval. */
 pspec_status pspec_hvp(pspec_graph* g, const void* U, const void* V, int k, double p,
                        pspec_dtype dtype, void* HV_out, unsigned flags, void* stream);
 
@@ -151,9 +169,10 @@ pspec_status pspec_hvp(pspec_graph* g, const void* U, const void* V, int k, doub
  * handle and column count k by timing them.  Candidates: the edges-per-lane
  * target L in {Q, 2Q, 4Q, 8Q, 16Q} (Q = column lanes per row for this k; a
  * row of degree d gets the smallest power-of-two number of edge slots E with
- * d <= L*E, so L fixes how many rows a warp task holds, 32/(E*Q)) and the
- * resident blocks per SM (the maximum the kernel's registers allow, and one
- * fewer).  Each candidate runs one untimed eval + HVP and then `reps` timed
+ * d <= L*E, so L fixes how many rows a warp task holds, 32/(E*Q), and whether
+ * the staged kernel -- for tasks short enough for its shared-memory buffers,
+ * L <= 8 at k = 4, 8, 16 -- or the direct one runs) and the resident blocks per SM
+ * (as many as each kernel fits, and one fewer than the direct kernel fits).  Each candidate runs one untimed eval + HVP and then `reps` timed
  * ones on U, V (device, n x k row-major FP32); the fastest is kept on the
  * handle for every later FP32 call with this k's column split (it changes
  * the summation order of the per-column sums, within the stated tolerance,
@@ -203,6 +222,52 @@ pspec_status pspec_tune(pspec_graph* g, const float* U, const float* V, int k, d
 pspec_status pspec_hvp_noalloc(int64_t n, const int64_t* rowptr, const int32_t* col,
                                const float* val, const float* U, const float* V, int k, double p,
                                float* HV_out, void* stream);
+
+/* ------------------------------------------------ row-partitioned runs ---
+ * One rank of a run that partitions the rows of W over several GPUs (each
+ * rank a process with its own GPU).  Every per-column quantity of Section 2
+ * is a sum over rows, so a rank sums its owned rows, the ranks add their
+ * sums, and each rank finishes its owned rows from the global sums:
+ *   1. the caller copies the rows of U (and V) its owned rows read but other
+ *      ranks own -- the halo -- into rows n_owned..n_local-1 of its block;
+ *   2. pspec_eval_partial / pspec_hvp_partial sum the owned rows: FP64
+ *      sums_out = N_r, D_r (2k values) or N_r, D_r, sigma_N_r, sigma_D_r (4k),
+ *      with N_r = 1/2 sum over owned i, all j of w_ij |d_ij|^p, D_r = sum over
+ *      owned i of |u_i|^p, sigma_N_r = sum over owned i of (Delta_p u)_i v_i,
+ *      sigma_D_r = sum over owned i of phi_p(u_i) v_i;
+ *   3. the caller adds sums_out over the ranks (an FP64 allreduce);
+ *   4. pspec_eval_finish / pspec_hvp_finish form F, the gradient or the
+ *      Hessian product (pspec_eval's and pspec_hvp's definitions) of the
+ *      owned rows from the added sums (sums_in, same layout).
+ * All blocks are device FP32, n_local x k row-major (owned rows first, then
+ * halo rows); outputs are written on the owned rows only.  sums_out, sums_in
+ * and F_out are device FP64.  The partial call leaves the rows Delta_p u of
+ * the owned rows in grad_out (eval) or the handle (HVP) for its finish call;
+ * a finish call must follow its partial call on the same stream.  Errors:
+ * INVALID_ARG (k, p, NULL, misalignment, aliasing, a handle that is not a
+ * shard, a finish without its partial), CUDA; ZERO_COLUMN and NONFINITE
+ * through the status word.  The paper scales one graph over CPU threads
+ * (Section 3.2); the row partition is this library's way to scale it over
+ * GPUs.
+ *
+ * pspec_graph_create_shard: the owned rows of W on this rank with column
+ * indices renumbered to local vertices: owned vertices 0..n_owned-1 (in
+ * their global order), halo vertices n_owned..n_local-1.  rowptr has
+ * n_owned + 1 entries; col in [0, n_local).  Host arrays only
+ * (PSPEC_HOST_PTRS required).  Same validation as pspec_graph_create.  A
+ * shard handle takes only the calls of this section and pspec_tune. */
+pspec_status pspec_graph_create_shard(int64_t n_owned, int64_t n_local, const int64_t* rowptr,
+                                      const int32_t* col, const void* val, pspec_dtype val_dtype,
+                                      unsigned flags, void* stream, pspec_graph** out);
+pspec_status pspec_eval_partial(pspec_graph* g, const float* U, int k, double p, float* grad_out,
+                                double* sums_out, void* stream);
+pspec_status pspec_eval_finish(pspec_graph* g, const float* U, int k, double p, const double* sums_in,
+                               double* F_out, float* grad_out, void* stream);
+pspec_status pspec_hvp_partial(pspec_graph* g, const float* U, const float* V, int k, double p,
+                               float* HV_out, double* sums_out, void* stream);
+/* flags: PSPEC_HVP_ALG1 for Algorithm 1's form (see pspec_hvp) */
+pspec_status pspec_hvp_finish(pspec_graph* g, const float* U, const float* V, int k, double p,
+                              const double* sums_in, float* HV_out, unsigned flags, void* stream);
 
 /* ---------------------------------------------------------------- solve ---
  * pspec_solve: minimise Eq. 1 while p is continued from 2 toward 1

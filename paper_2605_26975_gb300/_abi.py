@@ -27,6 +27,8 @@ PSPEC_F64 = 1
 PSPEC_HOST_PTRS = 0x1
 PSPEC_CHECK_SYMMETRY = 0x2
 PSPEC_HVP_ALG1 = 0x4
+PSPEC_KEEP_DELTA = 0x8
+PSPEC_DELTA_KEPT = 0x10
 PSPEC_HESSIAN_EXACT = 0
 PSPEC_HESSIAN_ALG1 = 1
 
@@ -77,6 +79,12 @@ _SIGS = {
     "pspec_hvp_noalloc": (C.c_int, [C.c_int64, _vp, _vp, _vp, _vp, _vp, C.c_int, C.c_double, _vp,
                                     _vp]),
     "pspec_tune": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_double, C.c_int, C.POINTER(TuneReport), _vp]),
+    "pspec_graph_create_shard": (C.c_int, [C.c_int64, C.c_int64, _vp, _vp, _vp, C.c_int, C.c_uint, _vp,
+                                           C.POINTER(_vp)]),
+    "pspec_eval_partial": (C.c_int, [_vp, _vp, C.c_int, C.c_double, _vp, _vp, _vp]),
+    "pspec_eval_finish": (C.c_int, [_vp, _vp, C.c_int, C.c_double, _vp, _vp, _vp, _vp]),
+    "pspec_hvp_partial": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_double, _vp, _vp, _vp]),
+    "pspec_hvp_finish": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_double, _vp, _vp, C.c_uint, _vp]),
     "pspec_set_timing": (C.c_int, [_vp, C.c_int]),
     "pspec_kernel_times": (C.c_int, [_vp, C.c_char_p, C.c_size_t]),
     "pspec_last_error": (C.c_char_p, []),

@@ -84,49 +84,56 @@ class Graph:
             pass
 
     # ------------------------------------------------------------ per call
-    def eval(self, U, p, grad_out=None, parts=False):
+    def eval(self, U, p, grad_out=None, parts=False, keep_delta=False):
         """(F, grad[, parts]): F a float64 CUDA tensor with one entry per graph
-        of the handle, parts [n_graphs * 2k] (each graph's N_1..N_k, D_1..D_k)."""
+        of the handle, parts [n_graphs * 2k] (each graph's N_1..N_k, D_1..D_k).
+        keep_delta=True keeps Delta_p u on the handle for hvp(..., delta_kept=True)
+        at the same U (FP32, single graph)."""
         U = _dev_block(U, "U", self.n)
         k = U.shape[1]
         G = self.n_graphs
         grad = torch.empty_like(U) if grad_out is None else grad_out
         F = torch.empty(G, dtype=torch.float64, device=U.device)
         P = torch.empty(G * 2 * k, dtype=torch.float64, device=U.device) if parts else None
+        flags = _abi.PSPEC_KEEP_DELTA if keep_delta else 0
         st = lib().pspec_eval(self._h, _ptr(U), k, float(p), _DT[U.dtype], _ptr(F), _ptr(grad),
-                              _ptr(P), 0, _stream())
+                              _ptr(P), flags, _stream())
         check(st, "pspec_eval")
         return (F, grad, P) if parts else (F, grad)
 
-    def hvp(self, U, V, p, out=None, alg1=False):
+    def hvp(self, U, V, p, out=None, alg1=False, delta_kept=False):
         """Exact Hessian of F_p at U applied to V; alg1=True leaves out the
-        rank-two terms (the sparse-plus-diagonal form of Algorithm 1)."""
+        rank-two terms (the sparse-plus-diagonal form of Algorithm 1);
+        delta_kept=True reuses the Delta_p u kept by eval(U, p, keep_delta=True)
+        (same tensor U, unchanged since)."""
         U = _dev_block(U, "U", self.n)
         V = _dev_block(V, "V", self.n)
         if V.shape != U.shape or V.dtype != U.dtype:
             raise ValueError("U and V must have the same shape and dtype")
         HV = torch.empty_like(U) if out is None else out
+        flags = (_abi.PSPEC_HVP_ALG1 if alg1 else 0) | (_abi.PSPEC_DELTA_KEPT if delta_kept else 0)
         st = lib().pspec_hvp(self._h, _ptr(U), _ptr(V), U.shape[1], float(p), _DT[U.dtype],
-                             _ptr(HV), _abi.PSPEC_HVP_ALG1 if alg1 else 0, _stream())
+                             _ptr(HV), flags, _stream())
         check(st, "pspec_hvp")
         return HV
 
-    def eval_host(self, U, p, grad_out):
+    def eval_host(self, U, p, grad_out, keep_delta=False):
         """pspec_eval with PSPEC_HOST_PTRS: U and grad_out are CPU tensors
         (pinned for asynchronous copies); returns F as a Python float (a list
         of floats, one per graph, for a batched handle)."""
         k = U.shape[1]
         F = (C.c_double * self.n_graphs)()
+        flags = _abi.PSPEC_HOST_PTRS | (_abi.PSPEC_KEEP_DELTA if keep_delta else 0)
         st = lib().pspec_eval(self._h, C.c_void_p(U.data_ptr()), k, float(p), _DT[U.dtype],
-                              F, C.c_void_p(grad_out.data_ptr()), None,
-                              _abi.PSPEC_HOST_PTRS, _stream())
+                              F, C.c_void_p(grad_out.data_ptr()), None, flags, _stream())
         check(st, "pspec_eval(host)")
         return F[0] if self.n_graphs == 1 else list(F)
 
-    def hvp_host(self, U, V, p, out):
+    def hvp_host(self, U, V, p, out, delta_kept=False):
+        flags = _abi.PSPEC_HOST_PTRS | (_abi.PSPEC_DELTA_KEPT if delta_kept else 0)
         st = lib().pspec_hvp(self._h, C.c_void_p(U.data_ptr()), C.c_void_p(V.data_ptr()),
                              U.shape[1], float(p), _DT[U.dtype], C.c_void_p(out.data_ptr()),
-                             _abi.PSPEC_HOST_PTRS, _stream())
+                             flags, _stream())
         check(st, "pspec_hvp(host)")
         return out
 
@@ -214,6 +221,75 @@ class Graph:
                 cnt, ms = rest.split(":")
                 out[name] = (int(cnt), float(ms))
         return out
+
+
+class Shard:
+    """One rank's rows of a row-partitioned W (pspec_graph_create_shard): the
+    owned rows' CSR with local columns (owned vertices first, halo after).
+    Its calls return partial FP64 sums for the caller to add over ranks, and
+    finish the owned rows from the added sums."""
+
+    def __init__(self, n_owned, n_local, rowptr, col, val):
+        rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        val = np.ascontiguousarray(val)
+        if val.dtype not in (np.float32, np.float64):
+            val = val.astype(np.float64)
+        vt = _abi.PSPEC_F32 if val.dtype == np.float32 else _abi.PSPEC_F64
+        h = C.c_void_p()
+        check(lib().pspec_graph_create_shard(int(n_owned), int(n_local), rowptr.ctypes.data, col.ctypes.data,
+                                             val.ctypes.data, vt, _abi.PSPEC_HOST_PTRS, _stream(),
+                                             C.byref(h)), "pspec_graph_create_shard")
+        self._h = h
+        self.n_owned, self.n_local = int(n_owned), int(n_local)
+
+    close = Graph.close
+    __del__ = Graph.__del__
+    status = Graph.status
+
+    @property
+    def handle(self):
+        return self._h
+
+    def _blocks(self, *ts):
+        for t in ts:
+            _dev_block(t, "block", self.n_local)
+            if t.dtype != torch.float32:
+                raise TypeError("the row-partitioned calls run the FP32 path")
+
+    def eval_partial(self, U, p, grad_out=None):
+        """(Delta_p u rows in grad_out, FP64 sums [N_r, D_r]) of the owned rows."""
+        self._blocks(U)
+        k = U.shape[1]
+        grad = torch.empty_like(U) if grad_out is None else grad_out
+        sums = torch.empty(2 * k, dtype=torch.float64, device=U.device)
+        check(lib().pspec_eval_partial(self._h, _ptr(U), k, float(p), _ptr(grad), _ptr(sums), _stream()),
+              "pspec_eval_partial")
+        return grad, sums
+
+    def eval_finish(self, U, p, sums, grad):
+        """(F, gradient of the owned rows) from the sums added over ranks."""
+        k = U.shape[1]
+        F = torch.empty(1, dtype=torch.float64, device=U.device)
+        check(lib().pspec_eval_finish(self._h, _ptr(U), k, float(p), _ptr(sums), _ptr(F), _ptr(grad),
+                                      _stream()), "pspec_eval_finish")
+        return F, grad
+
+    def hvp_partial(self, U, V, p, out=None):
+        """(sparse part of the owned rows in out, FP64 sums [N_r, D_r, sigma_N_r, sigma_D_r])."""
+        self._blocks(U, V)
+        k = U.shape[1]
+        HV = torch.empty_like(U) if out is None else out
+        sums = torch.empty(4 * k, dtype=torch.float64, device=U.device)
+        check(lib().pspec_hvp_partial(self._h, _ptr(U), _ptr(V), k, float(p), _ptr(HV), _ptr(sums),
+                                      _stream()), "pspec_hvp_partial")
+        return HV, sums
+
+    def hvp_finish(self, U, V, p, sums, HV, alg1=False):
+        """The Hessian product of the owned rows from the sums added over ranks."""
+        check(lib().pspec_hvp_finish(self._h, _ptr(U), _ptr(V), U.shape[1], float(p), _ptr(sums), _ptr(HV),
+                                     _abi.PSPEC_HVP_ALG1 if alg1 else 0, _stream()), "pspec_hvp_finish")
+        return HV
 
 
 def default_opts(**kw):

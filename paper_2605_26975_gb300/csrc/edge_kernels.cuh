@@ -6,7 +6,7 @@
 //           N = 1/2 sum_ij w_ij |u_i - u_j|^p,  D = sum_i |u_i|^p
 //  hvp:   additionally, for a direction V,
 //           S_i = sum_j w_ij |u_i - u_j|^(p-2) (v_i - v_j)      -> out_a
-//           Delta_i                                              -> out_b
+//           Delta_i                             -> out_b (skipped if NULL)
 //         and sigma_N = sum_i Delta_i v_i, sigma_D = sum_i phi_p(u_i) v_i.
 //
 // Arithmetic.  Every stored entry (i, j) costs one lg2 and one ex2 per column,
@@ -42,9 +42,10 @@
 
 namespace pspec {
 
-// Entries per lane per row before a row gets more edge slots: 8*Q, so a hub
-// chunk (32/Q slots x that) is 256 entries for every column split.
-__host__ __device__ constexpr int edges_per_lane(int Q) { return 8 * Q; }
+// Entries per lane per row before a row gets more edge slots, by default: 8,
+// so a task holds at most 256 / Q entries (a hub chunk is that long), which
+// fits the staged kernel's buffers for k = 4, 8 and 16 (edge_staged.cuh).
+__host__ __device__ constexpr int edges_per_lane(int /*Q*/) { return 8; }
 
 struct EdgeArgs {
   const int2* cw;         // degree-sorted entries: x = column, y = bits of log2 w
@@ -62,6 +63,7 @@ struct EdgeArgs {
   unsigned* hub_ticket;
   float p;
   float pm2;
+  double p64;  // p exactly, for the FP64 scalars and coefficients
   GridReduce gr;
   double* scalars;
   int* status;
@@ -71,7 +73,20 @@ struct EdgeArgs {
   float* task_part;
   // HVP in Algorithm 1's form: the epilogue's rank-two coefficient is zero
   int alg1;
+  // HVP with Delta_p u kept from the evaluation at the same U: that
+  // evaluation's N[16], D[16] (the staged kernel then sums only sigma_N and
+  // sigma_D); NULL otherwise
+  const double* keep_nd;
 };
+
+// What an edge kernel sums: the objective (N, D, Delta_p u), the Hessian
+// product (N, D, sigma_N, sigma_D, S, and Delta_p u unless out_b is NULL), or
+// the Hessian product at a point whose Delta_p u and N, D were kept by its
+// evaluation (sigma_N, sigma_D and S only).
+constexpr int kModeEval = 0, kModeHvp = 1, kModeHvpKept = 2;
+
+// Scalar slots of the per-call FP64 array (d_scalars)
+constexpr int kScN = 0, kScD = 16, kScCN = 32, kScCD = 48, kScF = 64, kScCoef = 80, kScKeep = 256;
 
 template <int K, int CPL, int VW>
 __device__ __forceinline__ void load_row(const float* base, int64_t row, int c0, float* dst) {
@@ -142,11 +157,19 @@ struct AccBank<CPL, NQ, COMP, false> {
 };
 
 // Resident blocks per SM the kernel is compiled for: with lanes of at most
-// four columns both kernels fit four blocks of 256 threads (64 registers)
-// without spilling, and the gathers' latency is hidden by that many warps.
-template <int K, bool HVP>
+// four columns the kernels fit four blocks of 256 threads (64 registers)
+// without spilling, and the Hessian product at a kept point (no |d|^p sum,
+// two column sums instead of four) fits five (48 registers) for k >= 8; the
+// gathers' latency is hidden by that many warps.
+template <int K, int MODE>
 __host__ __device__ constexpr int edge_min_blocks() {
   return K / q_of(K) <= 4 ? 4 : 1;
+}
+
+// Whether the direct kernel issues a task's first loads one task ahead (PF).
+template <int K, int MODE>
+__host__ __device__ constexpr bool edge_prefetch() {
+  return MODE == kModeHvpKept && K / q_of(K) <= 4;
 }
 
 // task descriptor fields (see ensure_tasks)
@@ -162,7 +185,7 @@ __device__ __forceinline__ bool task_is_hub(int4 t) { return ((t.z >> 8) & 1) !=
 //    phi = that * d.  A tie is selected away before the product (p < 2: no
 //    curvature term; p = 2: the term is w), so a large weight never meets
 //    inf * 0.
-template <int K, int CPL, int VW, bool HVP, int G>
+template <int K, int CPL, int VW, bool HVP, bool KEPT, int G>
 __device__ __forceinline__ void edge_group(const EdgeArgs& a, const int2 (&e)[G], int c0,
                                            const float (&ui)[CPL], const float (&vi)[CPL], float ex,
                                            bool zero_rule, float (&dsum)[CPL], float (&nsum)[CPL],
@@ -184,7 +207,7 @@ __device__ __forceinline__ void edge_group(const EdgeArgs& a, const int2 (&e)[G]
         const float sz = (zero_rule && d == 0.0f) ? 0.0f : sw;  // w |d|^(p-2)
         const float ph = sz * d;                                 // w phi_p(d)
         dsum[c] += ph;
-        nsum[c] = fmaf(ph, d, nsum[c]);
+        if constexpr (!KEPT) nsum[c] = fmaf(ph, d, nsum[c]);
         ssum[c] = fmaf(sz, vi[c] - vj[u][c], ssum[c]);
       } else {
         const float ph = copysignf(ex2_approx(fmaf(ex, lg2_approx(fabsf(d)), lw)), d);  // w phi_p(d)
@@ -195,18 +218,148 @@ __device__ __forceinline__ void edge_group(const EdgeArgs& a, const int2 (&e)[G]
   }
 }
 
+// Column c's FP64 scalars and epilogue coefficients from its sums N, D (and,
+// for the Hessian product, sigma_N, sigma_D) into the scalar array sc (slots
+// kSc*): the gradient's p/D and p lambda/D, or the Hessian product's
+// A = p(p-1)/D, lambda, B = p^2/D^2 (0 in Algorithm 1's form), sigma_D and
+// E = sigma_N - 2 lambda sigma_D.  Returns the status bits it found.
+__device__ __forceinline__ int column_scalars(int c, double N, double D, double sN, double sD, bool hvp,
+                                              double p, int alg1, double* sc) {
+  sc[kScN + c] = N;
+  sc[kScD + c] = D;
+  int flags = 0;
+  if (!isfinite(N) || !isfinite(D)) flags |= kStatusNonFinite;
+  else if (!(D > 0.0)) flags |= kStatusZeroColumn;
+  const double lam = N / D;
+  double* coef = sc + kScCoef;  // 6 x 16
+  if (hvp) {
+    sc[kScCN + c] = sN;
+    sc[kScCD + c] = sD;
+    if (!isfinite(sN) || !isfinite(sD)) flags |= kStatusNonFinite;
+    coef[0 * 16 + c] = p * (p - 1.0) / D;              // A
+    coef[1 * 16 + c] = lam;                            // lambda
+    coef[2 * 16 + c] = alg1 ? 0.0 : p * p / (D * D);  // B
+    coef[3 * 16 + c] = sD;                             // sigma_D
+    coef[4 * 16 + c] = sN - 2.0 * lam * sD;            // E
+  } else {
+    coef[0 * 16 + c] = p / D;
+    coef[1 * 16 + c] = p * lam / D;
+  }
+  return flags;
+}
+
+// The per-column sums of a launch, from each lane's float-float values v
+// (quantity qq of column c0 + c): lanes of equal q are added over the warp,
+// warps over the block and blocks over the grid, all in float-float and in a
+// fixed order; the last block then writes the FP64 scalars and the epilogue
+// coefficients.  Quantities: N, D (objective); N, D, sigma_N, sigma_D
+// (Hessian product); sigma_N, sigma_D with N, D from a.keep_nd (Hessian
+// product at a point whose Delta_p u was kept).
+template <int K, int NQ, bool HVP, bool KEPT, int CPL>
+__device__ __forceinline__ void finish_edges(float2 (&v)[NQ][CPL], const EdgeArgs& a) {
+  constexpr int Q = q_of(K);
+  constexpr int NV = NQ * K;
+  __shared__ float2 s_warp[kWarps][NV];
+  __shared__ float2 s_blk[NV];
+  __shared__ float2 s_tot[NV];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int c0 = (lane % Q) * CPL;
+#pragma unroll
+  for (int off = Q; off < 32; off <<= 1)
+#pragma unroll
+    for (int qq = 0; qq < NQ; ++qq)
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) v[qq][c] = ff_add(v[qq][c], shfl_xor_ff(v[qq][c], off));
+  if (lane < Q)
+#pragma unroll
+    for (int qq = 0; qq < NQ; ++qq)
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) s_warp[wib][qq * K + c0 + c] = v[qq][c];
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    float2 acc = make_float2(0.f, 0.f);
+    for (int w = 0; w < kWarps; ++w) acc = ff_add(acc, s_warp[w][threadIdx.x]);
+    s_blk[threadIdx.x] = acc;
+  }
+  __syncthreads();
+  if (!grid_reduce_ff<NV>(s_blk, s_tot, a.gr)) return;
+
+  // last block: FP64 scalars and epilogue coefficients
+  if (threadIdx.x < K) {
+    const int c = threadIdx.x;
+    double N, D;
+    if constexpr (KEPT) {
+      N = a.keep_nd[c];
+      D = a.keep_nd[16 + c];
+    } else {
+      N = 0.5 * ff_to_double(s_tot[c]);  // both triangles stored
+      D = ff_to_double(s_tot[K + c]);
+    }
+    double sN = 0.0, sD = 0.0;
+    if constexpr (HVP) {
+      constexpr int o = KEPT ? 0 : 2;  // sigma_N, sigma_D after N, D unless N, D are kept
+      sN = ff_to_double(s_tot[o * K + c]);
+      sD = ff_to_double(s_tot[(o + 1) * K + c]);
+    }
+    const int flags = column_scalars(c, N, D, sN, sD, HVP, a.p64, a.alg1, a.scalars);
+    if (flags) atomicOr(a.status, flags);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double F = 0.0;
+    for (int c = 0; c < K; ++c) F += a.scalars[kScN + c] / a.scalars[kScD + c];
+    a.scalars[kScF] = F;
+  }
+}
+
 template <int G>
 __device__ __forceinline__ void load_entries(const int2* __restrict__ cw, int E, int2 (&e)[G]) {
 #pragma unroll
   for (int u = 0; u < G; ++u) e[u] = __ldg(cw + u * E);
 }
 
-template <int K, bool HVP>
-__global__ void __launch_bounds__(kBlock, edge_min_blocks<K, HVP>()) edge_kernel(EdgeArgs a) {
+// A lane's part of a warp task (see ensure_tasks): its team (row) and edge
+// slot, its entries cw[start + slot + j E] for j < n_my, the sorted row whose
+// vertex perm[prow] it works on.
+struct LaneTask {
+  bool hub, active;
+  int elog, E, T, team, slot, cnt, start, n_my, prow;
+};
+
+template <int Q>
+__device__ __forceinline__ LaneTask lane_task(int4 task, int lane) {
+  LaneTask v;
+  v.hub = task_is_hub(task);
+  v.elog = task.z & 0xff;
+  v.E = 1 << v.elog;
+  v.T = v.E * Q;
+  v.team = lane / v.T;
+  v.slot = (lane % v.T) / Q;
+  if (!v.hub) {
+    const int deg = task.y >> 8;
+    v.active = v.team < (task.y & 0xff);
+    v.cnt = deg;
+    v.start = task.w + v.team * deg;
+  } else {
+    v.active = true;
+    v.cnt = task.z >> 10;
+    v.start = task.w;
+  }
+  v.n_my = (v.active && v.slot < v.cnt) ? ((v.cnt - v.slot + v.E - 1) >> v.elog) : 0;
+  v.prow = task.x + (v.hub ? 0 : v.team);
+  return v;
+}
+
+template <int K, int MODE>
+__global__ void __launch_bounds__(kBlock, edge_min_blocks<K, MODE>()) edge_kernel(EdgeArgs a) {
+  constexpr bool HVP = MODE != kModeEval;
+  constexpr bool KEPT = MODE == kModeHvpKept;
+  constexpr bool PF = edge_prefetch<K, MODE>();
   constexpr int Q = q_of(K);
   constexpr int CPL = K / Q;
   constexpr int VW = vw_of(K);
-  constexpr int NQ = HVP ? 4 : 2;  // N, D (, sigma_N, sigma_D)
+  constexpr int NQ = MODE == kModeHvp ? 4 : 2;  // N, D (, sigma_N, sigma_D) | sigma_N, sigma_D
   constexpr int NV = NQ * K;
   constexpr int UNR = HVP ? (CPL > 8 ? 1 : 2) : (CPL > 8 ? 2 : 4);  // entries per lane per step
   constexpr bool COMP = !HVP;
@@ -216,12 +369,8 @@ __global__ void __launch_bounds__(kBlock, edge_min_blocks<K, HVP>()) edge_kernel
 
   if (a.skip && *a.skip) return;  // uniform over the grid
   __shared__ float s_acc[SMEM_ACC ? Acc::kSlots * kBlock : 1];
-  __shared__ float2 s_warp[kWarps][NV];
-  __shared__ float2 s_blk[NV];
-  __shared__ float2 s_tot[NV];
 
   const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
   const int q = lane % Q;
   const int c0 = q * CPL;
   const int gwarp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
@@ -233,31 +382,49 @@ __global__ void __launch_bounds__(kBlock, edge_min_blocks<K, HVP>()) edge_kernel
   Acc acc;
   acc.init(s_acc);
 
-  for (int t = gwarp; t < a.n_tasks; t += nwarps) {
-    const int4 task = __ldg(&a.tasks[t]);
-    const bool hub = task_is_hub(task);
-    const int elog = task.z & 0xff;
-    const int E = 1 << elog;
-    const int T = E * Q;
-    const int team = lane / T;
-    const int slot = (lane % T) / Q;
-    int cnt, start;  // entries of this lane's row (or hub chunk) and the first of them
-    bool active;
-    if (!hub) {
-      const int deg = task.y >> 8;
-      active = team < (task.y & 0xff);
-      cnt = deg;
-      start = task.w + team * deg;
-    } else {
-      active = true;
-      cnt = task.z >> 10;
-      start = task.w;
+  // With PF the loads a task starts with -- its descriptor, its row's vertex
+  // and its first entries -- are issued one task ahead (the descriptor two
+  // ahead), so a task's chain of dependent loads starts at its own row and
+  // neighbour rows.
+  int4 pf_task = make_int4(0, 0, 0, 0), pf_next = make_int4(0, 0, 0, 0);
+  int pf_row = 0;
+  int2 pf_e[UNR];
+  if constexpr (PF) {
+    if (gwarp < a.n_tasks) {
+      pf_task = __ldg(&a.tasks[gwarp]);
+      const LaneTask v = lane_task<Q>(pf_task, lane);
+      if (v.active) pf_row = __ldg(&a.perm[v.prow]);
+      if (v.n_my >= UNR) load_entries<UNR>(a.cw + v.start + v.slot, v.E, pf_e);
     }
-    const int n_my = (active && slot < cnt) ? ((cnt - slot + E - 1) >> elog) : 0;
-    const int2* cw = a.cw + start + slot;  // this lane's entries: cw[j * E], j < n_my
+    if (gwarp + nwarps < a.n_tasks) pf_next = __ldg(&a.tasks[gwarp + nwarps]);
+  }
+
+  for (int t = gwarp; t < a.n_tasks; t += nwarps) {
+    const int4 task = PF ? pf_task : __ldg(&a.tasks[t]);
+    const LaneTask lt = lane_task<Q>(task, lane);
+    const bool hub = lt.hub;
+    const int elog = lt.elog, E = lt.E, T = lt.T, slot = lt.slot, n_my = lt.n_my;
+    const bool active = lt.active;
+    const int2* cw = a.cw + lt.start + slot;  // this lane's entries: cw[j * E], j < n_my
     int2 nx[UNR];
-    if (n_my >= UNR) load_entries<UNR>(cw, E, nx);
-    const int64_t row = active ? (int64_t)__ldg(&a.perm[task.x + (hub ? 0 : team)]) : 0;
+    int64_t row;
+    if constexpr (PF) {
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) nx[u] = pf_e[u];
+      row = active ? (int64_t)pf_row : 0;
+      // the next task's first loads, and the descriptor of the one after it
+      const int tn = t + nwarps;
+      pf_task = pf_next;
+      if (tn < a.n_tasks) {
+        const LaneTask v = lane_task<Q>(pf_task, lane);
+        if (v.active) pf_row = __ldg(&a.perm[v.prow]);
+        if (v.n_my >= UNR) load_entries<UNR>(a.cw + v.start + v.slot, v.E, pf_e);
+      }
+      if (tn + nwarps < a.n_tasks) pf_next = __ldg(&a.tasks[tn + nwarps]);
+    } else {
+      if (n_my >= UNR) load_entries<UNR>(cw, E, nx);
+      row = active ? (int64_t)__ldg(&a.perm[lt.prow]) : 0;
+    }
 
     float ui[CPL], vi[CPL], dsum[CPL], nsum[CPL], ssum[CPL];
 #pragma unroll
@@ -272,13 +439,13 @@ __global__ void __launch_bounds__(kBlock, edge_min_blocks<K, HVP>()) edge_kernel
 #pragma unroll
       for (int u = 0; u < UNR; ++u) e[u] = nx[u];
       if (j + 2 * UNR <= n_my) load_entries<UNR>(cw + (j + UNR) * E, E, nx);  // next step's entries
-      edge_group<K, CPL, VW, HVP, UNR>(a, e, c0, ui, vi, ex, zero_rule, dsum, nsum, ssum);
+      edge_group<K, CPL, VW, HVP, KEPT, UNR>(a, e, c0, ui, vi, ex, zero_rule, dsum, nsum, ssum);
     }
     if constexpr (UNR >= 4) {
       if (n_my - j >= 2) {
         int2 e[2];
         load_entries<2>(cw + j * E, E, e);
-        edge_group<K, CPL, VW, HVP, 2>(a, e, c0, ui, vi, ex, zero_rule, dsum, nsum, ssum);
+        edge_group<K, CPL, VW, HVP, KEPT, 2>(a, e, c0, ui, vi, ex, zero_rule, dsum, nsum, ssum);
         j += 2;
       }
     }
@@ -286,7 +453,7 @@ __global__ void __launch_bounds__(kBlock, edge_min_blocks<K, HVP>()) edge_kernel
       if (j < n_my) {  // at most one entry left
         int2 e[1];
         load_entries<1>(cw + j * E, E, e);
-        edge_group<K, CPL, VW, HVP, 1>(a, e, c0, ui, vi, ex, zero_rule, dsum, nsum, ssum);
+        edge_group<K, CPL, VW, HVP, KEPT, 1>(a, e, c0, ui, vi, ex, zero_rule, dsum, nsum, ssum);
       }
     }
     // row sums across the E edge slots of each team (lanes of equal q)
@@ -294,35 +461,40 @@ __global__ void __launch_bounds__(kBlock, edge_min_blocks<K, HVP>()) edge_kernel
 #pragma unroll
       for (int c = 0; c < CPL; ++c) {
         dsum[c] += __shfl_xor_sync(0xffffffffu, dsum[c], off);
-        nsum[c] += __shfl_xor_sync(0xffffffffu, nsum[c], off);
+        if constexpr (!KEPT) nsum[c] += __shfl_xor_sync(0xffffffffu, nsum[c], off);
         if constexpr (HVP) ssum[c] += __shfl_xor_sync(0xffffffffu, ssum[c], off);
       }
     }
     const bool lead = active && slot == 0;
     const bool first_chunk = !hub || ((task.z >> 9) & 1);
     // this task's contributions of this lane to the per-column sums
-    float tN[CPL], tD[CPL], tCN[CPL], tCD[CPL];
+    float tq[NQ][CPL];
 #pragma unroll
-    for (int c = 0; c < CPL; ++c) { tN[c] = 0.f; tD[c] = 0.f; tCN[c] = 0.f; tCD[c] = 0.f; }
+    for (int qq = 0; qq < NQ; ++qq)
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) tq[qq][c] = 0.f;
     if (lead) {
 #pragma unroll
-      for (int c = 0; c < CPL; ++c) tN[c] = nsum[c];
-      if (first_chunk) {  // vertex terms once per row
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-          const float phu = abs_pow_pm2_clamped(ui[c], pm2) * ui[c];  // phi_p(u_i)
-          tD[c] = phu * ui[c];                                        // |u_i|^p
-          if constexpr (HVP) tCD[c] = phu * vi[c];
+      for (int c = 0; c < CPL; ++c) {
+        float phu = 0.f;
+        if (first_chunk) phu = abs_pow_pm2_clamped(ui[c], pm2) * ui[c];  // phi_p(u_i), once per row
+        if constexpr (MODE == kModeEval) {
+          tq[0][c] = nsum[c];
+          tq[1][c] = phu * ui[c];  // |u_i|^p
+        } else if constexpr (MODE == kModeHvp) {
+          tq[0][c] = nsum[c];
+          tq[1][c] = phu * ui[c];
+          tq[2][c] = dsum[c] * vi[c];  // sigma_N: a row's Delta_i v_i, or a chunk's share
+          tq[3][c] = phu * vi[c];      // sigma_D
+        } else {
+          tq[0][c] = dsum[c] * vi[c];
+          tq[1][c] = phu * vi[c];
         }
       }
-      // sigma_N: a whole row's Delta_i v_i, or a chunk's share of it
-#pragma unroll
-      for (int c = 0; c < CPL; ++c)
-        if constexpr (HVP) tCN[c] = dsum[c] * vi[c];
       if (!hub) {
         if constexpr (HVP) {
           store_row<K, CPL, VW>(a.out_a, row, c0, ssum);
-          store_row<K, CPL, VW>(a.out_b, row, c0, dsum);
+          if (a.out_b) store_row<K, CPL, VW>(a.out_b, row, c0, dsum);
         } else {
           store_row<K, CPL, VW>(a.out_a, row, c0, dsum);
         }
@@ -331,39 +503,24 @@ __global__ void __launch_bounds__(kBlock, edge_min_blocks<K, HVP>()) edge_kernel
     if (!a.task_part) {
       if (lead) {
 #pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-          acc.add(0, c, tN[c]);
-          acc.add(1, c, tD[c]);
-          if constexpr (HVP) {
-            acc.add(2, c, tCN[c]);
-            acc.add(3, c, tCD[c]);
-          }
-        }
+        for (int qq = 0; qq < NQ; ++qq)
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) acc.add(qq, c, tq[qq][c]);
       }
     } else {
       // one graph of a batch: fold the task's sums over the warp (lanes of
       // equal q) and publish them in the task's slot
       for (int off = Q; off < 32; off <<= 1)
 #pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-          tN[c] += __shfl_xor_sync(0xffffffffu, tN[c], off);
-          tD[c] += __shfl_xor_sync(0xffffffffu, tD[c], off);
-          if constexpr (HVP) {
-            tCN[c] += __shfl_xor_sync(0xffffffffu, tCN[c], off);
-            tCD[c] += __shfl_xor_sync(0xffffffffu, tCD[c], off);
-          }
-        }
+        for (int qq = 0; qq < NQ; ++qq)
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) tq[qq][c] += __shfl_xor_sync(0xffffffffu, tq[qq][c], off);
       if (lane < Q) {
         float* tp = a.task_part + (size_t)t * NV;
 #pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-          tp[c0 + c] = tN[c];
-          tp[K + c0 + c] = tD[c];
-          if constexpr (HVP) {
-            tp[2 * K + c0 + c] = tCN[c];
-            tp[3 * K + c0 + c] = tCD[c];
-          }
-        }
+        for (int qq = 0; qq < NQ; ++qq)
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) tp[qq * K + c0 + c] = tq[qq][c];
       }
     }
     if (hub) {
@@ -406,7 +563,7 @@ __global__ void __launch_bounds__(kBlock, edge_min_blocks<K, HVP>()) edge_kernel
           for (int c = 0; c < CPL; ++c) { rd[c] = td[c].s - td[c].c; rs[c] = ts[c].s - ts[c].c; }
           if constexpr (HVP) {
             store_row<K, CPL, VW>(a.out_a, row, c0, rs);
-            store_row<K, CPL, VW>(a.out_b, row, c0, rd);
+            if (a.out_b) store_row<K, CPL, VW>(a.out_b, row, c0, rd);
           } else {
             store_row<K, CPL, VW>(a.out_a, row, c0, rd);
           }
@@ -416,73 +573,12 @@ __global__ void __launch_bounds__(kBlock, edge_min_blocks<K, HVP>()) edge_kernel
     }
   }
   if (a.task_part) return;  // batches: per-graph sums are reduced by batch_reduce
-
-  // warp: lanes of equal q in float-float; lanes 0..Q-1 hold the warp sums
-  {
-    float2 v[NQ][CPL];
+  float2 v[NQ][CPL];
 #pragma unroll
-    for (int c = 0; c < CPL; ++c) {
+  for (int c = 0; c < CPL; ++c)
 #pragma unroll
-      for (int qq = 0; qq < NQ; ++qq) v[qq][c] = acc.ff(qq, c);
-    }
-#pragma unroll
-    for (int off = Q; off < 32; off <<= 1)
-#pragma unroll
-      for (int qq = 0; qq < NQ; ++qq)
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) v[qq][c] = ff_add(v[qq][c], shfl_xor_ff(v[qq][c], off));
-    if (lane < Q)
-#pragma unroll
-      for (int qq = 0; qq < NQ; ++qq)
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) s_warp[wib][qq * K + c0 + c] = v[qq][c];
-  }
-  __syncthreads();
-  if (threadIdx.x < NV) {
-    float2 acc = make_float2(0.f, 0.f);
-    for (int w = 0; w < kWarps; ++w) acc = ff_add(acc, s_warp[w][threadIdx.x]);
-    s_blk[threadIdx.x] = acc;
-  }
-  __syncthreads();
-  if (!grid_reduce_ff<NV>(s_blk, s_tot, a.gr)) return;
-
-  // last block: FP64 scalars and epilogue coefficients
-  if (threadIdx.x < K) {
-    const int c = threadIdx.x;
-    const double N = 0.5 * ff_to_double(s_tot[c]);  // both triangles stored
-    const double D = ff_to_double(s_tot[K + c]);
-    double* sc = a.scalars;
-    sc[0 + c] = N;   // kSlotN
-    sc[16 + c] = D;  // kSlotD
-    int flags = 0;
-    if (!isfinite(N) || !isfinite(D)) flags |= kStatusNonFinite;
-    else if (!(D > 0.0)) flags |= kStatusZeroColumn;
-    const double p = (double)a.p;
-    const double lam = N / D;
-    double* coef = sc + 80;  // kSlotCoef: 6 x 16
-    if constexpr (HVP) {
-      const double sN = ff_to_double(s_tot[2 * K + c]);
-      const double sD = ff_to_double(s_tot[3 * K + c]);
-      sc[32 + c] = sN;
-      sc[48 + c] = sD;
-      if (!isfinite(sN) || !isfinite(sD)) flags |= kStatusNonFinite;
-      coef[0 * 16 + c] = p * (p - 1.0) / D;  // A
-      coef[1 * 16 + c] = lam;                // lambda
-      coef[2 * 16 + c] = a.alg1 ? 0.0 : p * p / (D * D);  // B
-      coef[3 * 16 + c] = sD;                 // sigma_D
-      coef[4 * 16 + c] = sN - 2.0 * lam * sD;
-    } else {
-      coef[0 * 16 + c] = p / D;
-      coef[1 * 16 + c] = p * lam / D;
-    }
-    if (flags) atomicOr(a.status, flags);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double F = 0.0;
-    for (int c = 0; c < K; ++c) F += a.scalars[c] / a.scalars[16 + c];
-    a.scalars[64] = F;  // kSlotF
-  }
+    for (int qq = 0; qq < NQ; ++qq) v[qq][c] = acc.ff(qq, c);
+  finish_edges<K, NQ, HVP, KEPT>(v, a);
 }
 
 }  // namespace pspec

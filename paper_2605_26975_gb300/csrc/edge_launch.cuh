@@ -1,26 +1,68 @@
 // Host launcher of the fused edge kernels for one column count K; explicit
-// instantiations live in edge_k*.cu so the 32 kernels compile in parallel.
+// instantiations live in edge_k*.cu so the kernels compile in parallel.
+//
+// Two kernels compute the same sums: the staged kernel (edge_staged.cuh),
+// used whenever a task's entries fit its shared-memory buffers (entries per
+// task 32 L / Q <= staged_max_entries(K)), and the direct kernel
+// (edge_kernels.cuh) for longer tasks.  The edges-per-lane target L of the
+// handle's task set -- set by pspec_tune or PSPEC_EDGES_PER_LANE -- thus also
+// picks the kernel.
 #pragma once
 
 #include <algorithm>
 #include <cstdlib>
 
 #include "edge_kernels.cuh"
+#include "edge_staged.cuh"
 #include "internal.h"
 
 namespace pspec {
+
+inline int env_blocks_per_sm(int occ) {
+  if (const char* env = std::getenv("PSPEC_EDGE_BLOCKS_PER_SM")) return std::max(1, std::min(occ, std::atoi(env)));
+  return occ;
+}
+
+template <int K, int MODE>
+pspec_status launch_staged(pspec_graph* g, const EdgeArgs& a, int max_entries, int want, cudaStream_t s) {
+  // the largest dynamic shared memory this instantiation is ever given, set
+  // once per process (thread-safe initialisation)
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(edge_staged_kernel<K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(kWarps * staged_warp_bytes(K, MODE, staged_max_entries(K))));
+  PSPEC_CUDA(attr);
+  const size_t bytes = kWarps * staged_warp_bytes(K, MODE, max_entries);
+  int occ = 0;
+  PSPEC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, edge_staged_kernel<K, MODE>, kBlock, bytes));
+  occ = env_blocks_per_sm(std::max(occ, 1));
+  int blocks = grid_blocks(g, want > 0 ? std::min(want, occ) : occ);
+  blocks = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, ((int64_t)a.n_tasks + kWarps - 1) / kWarps));
+  edge_staged_kernel<K, MODE><<<blocks, kBlock, bytes, s>>>(a, max_entries);
+  PSPEC_CUDA(cudaGetLastError());
+  return PSPEC_OK;
+}
+
+template <int K, int MODE>
+pspec_status launch_direct(pspec_graph* g, const EdgeArgs& a, int64_t n_tasks, int want, cudaStream_t s) {
+  // resident blocks at the kernel's register count, once per process
+  static const int occ_direct = [] {
+    int o = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, edge_kernel<K, MODE>, kBlock, 0) != cudaSuccess) o = 1;
+    return std::max(o, 1);
+  }();
+  const int occ = env_blocks_per_sm(occ_direct);
+  int blocks = grid_blocks(g, want > 0 ? std::min(want, occ) : occ);
+  blocks = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (n_tasks + kWarps - 1) / kWarps));
+  edge_kernel<K, MODE><<<blocks, kBlock, 0, s>>>(a);
+  PSPEC_CUDA(cudaGetLastError());
+  return PSPEC_OK;
+}
 
 template <int K, bool HVP>
 pspec_status launch_edges_k(pspec_graph* g, const EdgeLaunch& L, cudaStream_t s) {
   constexpr int Q = q_of(K);
   PSPEC_TRY(ensure_tasks(g, Q));
   const TaskSet& ts = g->tasks[q_index(Q)];
-  static int occ = -1;
-  if (occ < 0) {
-    PSPEC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, edge_kernel<K, HVP>, kBlock, 0));
-    occ = std::max(occ, 1);
-    if (const char* env = std::getenv("PSPEC_EDGE_BLOCKS_PER_SM")) occ = std::max(1, std::min(occ, std::atoi(env)));
-  }
   EdgeArgs a;
   a.cw = g->d_cw_s;
   a.perm = g->d_perm;
@@ -35,8 +77,9 @@ pspec_status launch_edges_k(pspec_graph* g, const EdgeLaunch& L, cudaStream_t s)
   a.hub_nchunk = ts.d_hub_nchunk;
   a.chunk_hub = ts.d_chunk_hub;
   a.hub_ticket = ts.d_hub_ticket;
-  a.p = L.p;
-  a.pm2 = L.p - 2.0f;
+  a.p = (float)L.p;
+  a.pm2 = (float)L.p - 2.0f;
+  a.p64 = L.p;
   a.gr.block_part = g->d_block_part;
   a.gr.group_part = g->d_group_part;
   a.gr.counters = g->d_counters;
@@ -45,18 +88,24 @@ pspec_status launch_edges_k(pspec_graph* g, const EdgeLaunch& L, cudaStream_t s)
   a.skip = L.skip;
   a.task_part = L.task_part;
   a.alg1 = L.alg1 ? 1 : 0;
+  a.keep_nd = L.keep_nd;
   const int want = g->edge_blocks_per_sm[q_index(Q)];
-  int blocks = grid_blocks(g, want > 0 ? std::min(want, occ) : occ);
-  blocks = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (ts.n_tasks + kWarps - 1) / kWarps));
   TimedScope timer(g, HVP ? "hvp_edges" : "eval_edges", s);
-  edge_kernel<K, HVP><<<blocks, kBlock, 0, s>>>(a);
-  PSPEC_CUDA(cudaGetLastError());
-  return PSPEC_OK;
+  const int max_entries = ts.chunk_edges;  // 32 L / Q
+  if (max_entries <= staged_max_entries(K)) {
+    if constexpr (!HVP) return launch_staged<K, kModeEval>(g, a, max_entries, want, s);
+    else if (L.keep_nd) return launch_staged<K, kModeHvpKept>(g, a, max_entries, want, s);
+    else return launch_staged<K, kModeHvp>(g, a, max_entries, want, s);
+  }
+  if constexpr (!HVP) return launch_direct<K, kModeEval>(g, a, ts.n_tasks, want, s);
+  else if (L.keep_nd) return launch_direct<K, kModeHvpKept>(g, a, ts.n_tasks, want, s);
+  else return launch_direct<K, kModeHvp>(g, a, ts.n_tasks, want, s);
 }
 
 template <int K, bool HVP>
 pspec_status occupancy_k(int* blocks_per_sm) {
-  PSPEC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, edge_kernel<K, HVP>, kBlock, 0));
+  PSPEC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      blocks_per_sm, edge_kernel<K, HVP ? kModeHvp : kModeEval>, kBlock, 0));
   return PSPEC_OK;
 }
 

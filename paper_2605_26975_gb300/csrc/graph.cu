@@ -129,7 +129,7 @@ pspec_status ensure_tasks(pspec_graph* g, int Q) {
   const int64_t hub_deg = (int64_t)L * max_slots;
   const int chunk = L * max_slots;
   const std::vector<int64_t>& rp = g->h_rowptr_s;
-  const int64_t n = g->n;
+  const int64_t n = g->n_owned;  // a shard's halo rows (sorted last) get no tasks
   std::vector<int4> tasks;
   tasks.reserve((size_t)(n / 8 + 16));
   std::vector<int32_t> hub_row, hub_first, hub_nchunk, chunk_hub;
@@ -184,6 +184,7 @@ pspec_status ensure_tasks(pspec_graph* g, int Q) {
   }
   for (size_t q = gi + 1; q < graph_task.size(); ++q) graph_task[q] = (int32_t)tasks.size();
   ts.Q = Q;
+  ts.L = L;
   ts.chunk_edges = chunk;
   ts.n_tasks = (int64_t)tasks.size();
   ts.n_hubs = (int)hub_row.size();
@@ -279,7 +280,8 @@ static bool weights_ok(const T* v, int64_t nnz, std::string* why) {
 
 static pspec_status create_impl(int64_t n, const int64_t* rowptr_in, const int32_t* col_in,
                                 const void* val_in, pspec_dtype vt, unsigned flags, cudaStream_t s,
-                                const std::vector<int64_t>& node_off, pspec_graph** out) {
+                                const std::vector<int64_t>& node_off, pspec_graph** out,
+                                int64_t n_owned = -1) {
   if (!out) return set_error(PSPEC_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (n < 1 || n >= (int64_t)1 << 31) return set_error(PSPEC_ERR_INVALID_ARG, "n must be in [1, 2^31)");
@@ -297,6 +299,8 @@ static pspec_status create_impl(int64_t n, const int64_t* rowptr_in, const int32
     PSPEC_CUDA(cudaMemcpy(rp.data(), rowptr_in, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost));
   }
   if (rp[0] != 0) return set_error(PSPEC_ERR_INVALID_ARG, "rowptr[0] must be 0");
+  const bool shard = n_owned >= 0;
+  if (!shard) n_owned = n;
   for (int64_t i = 0; i < n; ++i)
     if (rp[i + 1] < rp[i]) return set_error(PSPEC_ERR_INVALID_ARG, "rowptr decreases at row " + std::to_string(i));
   const int64_t nnz = rp[n];
@@ -360,6 +364,8 @@ static pspec_status create_impl(int64_t n, const int64_t* rowptr_in, const int32
   cudaGetDevice(&g->device);
   cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, g->device);
   g->n = n;
+  g->n_owned = n_owned;
+  g->is_shard = shard;
   g->nnz = nnz;
   g->h_rowptr = std::move(rp);
   g->h_node_off = node_off;
@@ -414,8 +420,12 @@ static pspec_status create_impl(int64_t n, const int64_t* rowptr_in, const int32
     // rows of each graph of a batch stay within the graph's range
     std::vector<int64_t> gb = node_off;
     if (gb.empty()) gb = {0, n};
+    // (a shard's halo vertices, rows without entries, go after every owned
+    // row, so the owned rows are the first n_owned sorted rows)
     for (size_t q = 0; q + 1 < gb.size(); ++q)
       std::stable_sort(perm.begin() + gb[q], perm.begin() + gb[q + 1], [&](int32_t a, int32_t b) {
+        const bool ha = a >= n_owned, hb = b >= n_owned;
+        if (ha != hb) return hb;
         return rp0[a + 1] - rp0[a] < rp0[b + 1] - rp0[b];
       });
     std::vector<int64_t> rps(n + 1, 0);
@@ -480,6 +490,20 @@ pspec_status pspec_graph_create_batched(int32_t n_graphs, const int64_t* node_of
   return create_impl(off[n_graphs], rowptr, col, val, val_dtype, flags, (cudaStream_t)stream, off, out);
 }
 
+pspec_status pspec_graph_create_shard(int64_t n_owned, int64_t n_local, const int64_t* rowptr,
+                                      const int32_t* col, const void* val, pspec_dtype val_dtype,
+                                      unsigned flags, void* stream, pspec_graph** out) {
+  if (out) *out = nullptr;
+  if (!(flags & PSPEC_HOST_PTRS))
+    return set_error(PSPEC_ERR_INVALID_ARG, "pspec_graph_create_shard takes host arrays (PSPEC_HOST_PTRS)");
+  if (n_owned < 1 || n_local < n_owned) return set_error(PSPEC_ERR_INVALID_ARG, "need 1 <= n_owned <= n_local");
+  if (!rowptr) return set_error(PSPEC_ERR_INVALID_ARG, "rowptr is NULL");
+  // the halo rows carry no entries: extend the row offsets over them
+  std::vector<int64_t> rp(rowptr, rowptr + n_owned + 1);
+  rp.resize(n_local + 1, rp[n_owned]);
+  return create_impl(n_local, rp.data(), col, val, val_dtype, flags, (cudaStream_t)stream, {}, out, n_owned);
+}
+
 void pspec_graph_destroy(pspec_graph* g) {
   if (!g) return;
   for (pspec_graph* sub : g->subs) pspec_graph_destroy(sub);
@@ -498,6 +522,7 @@ void pspec_graph_destroy(pspec_graph* g) {
   cudaFree(g->d_graph_scalars);
   cudaFree(g->d_task_part);
   cudaFree(g->d_scratch);
+  cudaFree(g->d_delta_keep);
   cudaFree(g->d_hub_part);
   if (g->solve_stream) cudaStreamDestroy(g->solve_stream);
   if (g->h_solve_rec) cudaFreeHost(g->h_solve_rec);

@@ -57,7 +57,7 @@ struct NaArgs {
   float* delta;  // scratch
   int64_t n;
   float pm2;
-  float p;
+  double p;  // exactly as passed (the FP64 coefficients use it)
   GridReduce gr;
   double* coef;  // scratch: A, lambda, B, sigma_D, E per column (5 x 16)
 };
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kBlock) na_hvp_edges(NaArgs a) {
     const double D = ff_to_double(s_tot[K + c]);
     const double sN = ff_to_double(s_tot[2 * K + c]);
     const double sD = ff_to_double(s_tot[3 * K + c]);
-    const double p = (double)a.p, lam = N / D;
+    const double p = a.p, lam = N / D;
     a.coef[0 * 16 + c] = p * (p - 1.0) / D;
     a.coef[1 * 16 + c] = lam;
     a.coef[2 * 16 + c] = p * p / (D * D);
@@ -276,7 +276,7 @@ extern "C" pspec_status pspec_hvp_noalloc(int64_t n, const int64_t* rowptr, cons
   a.S = HV_out;
   a.delta = reinterpret_cast<float*>(sb + kOffDelta);
   a.n = n;
-  a.p = (float)p;
+  a.p = p;
   a.pm2 = (float)p - 2.0f;
   a.gr.block_part = reinterpret_cast<float2*>(sb + kOffBlock);
   a.gr.group_part = reinterpret_cast<float2*>(sb + kOffGroup);

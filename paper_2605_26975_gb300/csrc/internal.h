@@ -24,7 +24,8 @@ namespace pspec {
 struct TaskSet {
   bool built = false;
   int Q = 0;
-  int chunk_edges = 0;
+  int L = 0;            // edges-per-lane target the set was built with
+  int chunk_edges = 0;  // = most entries of one task, 32 L / Q
   int64_t n_tasks = 0;
   int n_hubs = 0;
   int n_chunks = 0;
@@ -53,6 +54,11 @@ struct Timing {
 
 struct pspec_graph {
   int64_t n = 0, nnz = 0;
+  // rows the edge kernels and epilogues cover: n, or for a shard of a
+  // row-partitioned graph its owned rows (the first n_owned local vertices;
+  // the rest are halo vertices, read only as neighbours)
+  int64_t n_owned = 0;
+  bool is_shard = false;
   int32_t n_graphs = 1;
   int device = 0;
   int sm_count = 0;
@@ -86,6 +92,14 @@ struct pspec_graph {
   // workspace
   float* d_scratch = nullptr;        // n x 16 floats (HVP's Delta rows)
   size_t scratch_elems = 0;
+  // Delta_p u kept by pspec_eval(PSPEC_KEEP_DELTA) for pspec_hvp(PSPEC_DELTA_KEPT)
+  float* d_delta_keep = nullptr;     // n x k floats
+  size_t delta_keep_elems = 0;
+  bool keep_valid = false;
+  const void* keep_U = nullptr;      // the U pointer as passed (host or device)
+  unsigned keep_host = 0;            // PSPEC_HOST_PTRS of that call
+  int keep_k = 0;
+  double keep_p = 0.0;
   float* d_hub_part = nullptr;       // [max chunks][2*16] partial row sums
   size_t hub_part_elems = 0;
   float2* d_block_part = nullptr;    // [max blocks][64]
@@ -163,12 +177,13 @@ struct EdgeLaunch {
   const float* U;
   const float* V;      // HVP only
   float* out_a;        // eval: Delta; HVP: sparse part S
-  float* out_b;        // HVP: Delta
-  float p;
+  float* out_b;        // HVP: Delta (NULL: not stored)
+  double p;
   int k;
   const int* skip = nullptr;  // device flag: when nonzero the launch does nothing
   float* task_part = nullptr; // batches: per-task column sums (see edge_kernels.cuh)
   bool alg1 = false;          // HVP: Algorithm 1's form (no rank-two terms)
+  const double* keep_nd = nullptr;  // HVP at a kept point: its N[16], D[16]
 };
 pspec_status edge_occupancy(int k, bool hvp, int* blocks_per_sm);
 pspec_status launch_eval_edges(pspec_graph* g, const EdgeLaunch& a, cudaStream_t s);
@@ -182,9 +197,18 @@ pspec_status hvp_plain64(pspec_graph* g, const double* U, const double* V, int k
 
 // FP32 fast path, device pointers only
 pspec_status eval_fast(pspec_graph* g, const float* U, int k, double p, double* F_out,
-                       float* grad, double* parts, cudaStream_t s);
+                       float* grad, double* parts, cudaStream_t s, bool keep_delta = false);
 pspec_status hvp_fast(pspec_graph* g, const float* U, const float* V, int k, double p, float* HV,
-                      cudaStream_t s, const int* skip = nullptr, bool alg1 = false);
+                      cudaStream_t s, const int* skip = nullptr, bool alg1 = false,
+                      bool delta_kept = false);
+// the epilogues over the handle's n_owned rows: grad from the Delta rows Dl
+// (in place when Dl == grad), HV over the sparse part S held in HV; the
+// coefficients come from d_scalars
+pspec_status run_grad_epilogue(pspec_graph* g, const float* U, const float* Dl, float* grad, int k, double p,
+                               cudaStream_t s);
+pspec_status run_hvp_epilogue(pspec_graph* g, const float* U, const float* V, const float* Dl, float* HV,
+                              int k, double p, cudaStream_t s, const int* skip = nullptr);
+pspec_status ensure_scratch(pspec_graph* g, size_t elems);
 // the edge kernel of hvp_fast alone: S (sparse part) into S, Delta_p u into
 // the handle's scratch block, the epilogue coefficients into d_scalars
 pspec_status hvp_edges_fast(pspec_graph* g, const float* U, const float* V, int k, double p, float* S,
@@ -212,5 +236,6 @@ constexpr int kSlotCN = 32;    // [16] sum_i Delta_i V_i
 constexpr int kSlotCD = 48;    // [16] sum_i phi_p(u_i) V_i
 constexpr int kSlotF = 64;     // [1]
 constexpr int kSlotCoef = 80;  // [6*16] epilogue coefficients
+constexpr int kSlotKeep = 256; // [32] N, D of the last PSPEC_KEEP_DELTA evaluation
 
 }  // namespace pspec

@@ -51,10 +51,11 @@ pspec_status launch_hvp_edges(pspec_graph* g, const EdgeLaunch& L, cudaStream_t 
   return dispatch_edges<true>(g, L, s);
 }
 
-// grad = (p/D) Delta - (p lambda / D) phi_p(u), in place over Delta.
+// grad = (p/D) Delta - (p lambda / D) phi_p(u), from the rows Delta into G
+// (the same buffer: in place).
 template <int VW>
-__global__ void __launch_bounds__(256) grad_epilogue(const float* __restrict__ U, float* G,
-                                                     int64_t n_elems, int K,
+__global__ void __launch_bounds__(256) grad_epilogue(const float* __restrict__ U, const float* Dl,
+                                                     float* G, int64_t n_elems, int K,
                                                      const double* __restrict__ scalars, float pm2) {
   __shared__ float sA[kMaxK], sB[kMaxK];
   if (threadIdx.x < K) {
@@ -68,13 +69,13 @@ __global__ void __launch_bounds__(256) grad_epilogue(const float* __restrict__ U
     float u[VW], d[VW];
     load_vec<VW>(U + v * VW, u);
     if constexpr (VW == 4) {
-      float4 t = *reinterpret_cast<const float4*>(G + v * VW);
+      float4 t = *reinterpret_cast<const float4*>(Dl + v * VW);
       d[0] = t.x; d[1] = t.y; d[2] = t.z; d[3] = t.w;
     } else if constexpr (VW == 2) {
-      float2 t = *reinterpret_cast<const float2*>(G + v * VW);
+      float2 t = *reinterpret_cast<const float2*>(Dl + v * VW);
       d[0] = t.x; d[1] = t.y;
     } else {
-      d[0] = G[v];
+      d[0] = Dl[v];
     }
     const int c = (int)((v * VW) % K);
 #pragma unroll
@@ -138,22 +139,64 @@ static int epi_blocks(pspec_graph* g, int64_t nvec) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)g->sm_count * 8));
 }
 
-pspec_status eval_fast(pspec_graph* g, const float* U, int k, double p, double* F_out, float* grad,
-                       double* parts, cudaStream_t s) {
-  EdgeLaunch L{U, nullptr, grad, nullptr, (float)p, k};
-  PSPEC_TRY(launch_eval_edges(g, L, s));
-  const int64_t ne = g->n * k;
-  const float pm2 = (float)p - 2.0f;
-  {
-    TimedScope timer(g, "grad_epilogue", s);
-    if (k % 4 == 0)
-      grad_epilogue<4><<<epi_blocks(g, ne / 4), 256, 0, s>>>(U, grad, ne, k, g->d_scalars, pm2);
-    else if (k % 2 == 0)
-      grad_epilogue<2><<<epi_blocks(g, ne / 2), 256, 0, s>>>(U, grad, ne, k, g->d_scalars, pm2);
-    else
-      grad_epilogue<1><<<epi_blocks(g, ne), 256, 0, s>>>(U, grad, ne, k, g->d_scalars, pm2);
-    PSPEC_CUDA(cudaGetLastError());
+static pspec_status ensure_delta_keep(pspec_graph* g, size_t elems) {
+  if (g->delta_keep_elems >= elems) return PSPEC_OK;
+  if (g->d_delta_keep) cudaFree(g->d_delta_keep);
+  g->d_delta_keep = nullptr;
+  g->delta_keep_elems = 0;
+  g->keep_valid = false;
+  if (cudaMalloc(&g->d_delta_keep, sizeof(float) * elems) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(PSPEC_ERR_OOM, "device allocation of the kept Delta_p u rows failed");
   }
+  g->delta_keep_elems = elems;
+  return PSPEC_OK;
+}
+
+pspec_status run_grad_epilogue(pspec_graph* g, const float* U, const float* Dl, float* grad, int k, double p,
+                               cudaStream_t s) {
+  const int64_t ne = g->n_owned * k;
+  const float pm2 = (float)p - 2.0f;
+  TimedScope timer(g, "grad_epilogue", s);
+  if (k % 4 == 0)
+    grad_epilogue<4><<<epi_blocks(g, ne / 4), 256, 0, s>>>(U, Dl, grad, ne, k, g->d_scalars, pm2);
+  else if (k % 2 == 0)
+    grad_epilogue<2><<<epi_blocks(g, ne / 2), 256, 0, s>>>(U, Dl, grad, ne, k, g->d_scalars, pm2);
+  else
+    grad_epilogue<1><<<epi_blocks(g, ne), 256, 0, s>>>(U, Dl, grad, ne, k, g->d_scalars, pm2);
+  PSPEC_CUDA(cudaGetLastError());
+  return PSPEC_OK;
+}
+
+pspec_status run_hvp_epilogue(pspec_graph* g, const float* U, const float* V, const float* Dl, float* HV,
+                              int k, double p, cudaStream_t s, const int* skip) {
+  const int64_t ne = g->n_owned * k;
+  const float pm2 = (float)p - 2.0f;
+  TimedScope timer(g, "hvp_epilogue", s);
+  if (k % 4 == 0)
+    hvp_epilogue<4><<<epi_blocks(g, ne / 4), 256, 0, s>>>(U, V, Dl, HV, ne, k, g->d_scalars, pm2, skip);
+  else if (k % 2 == 0)
+    hvp_epilogue<2><<<epi_blocks(g, ne / 2), 256, 0, s>>>(U, V, Dl, HV, ne, k, g->d_scalars, pm2, skip);
+  else
+    hvp_epilogue<1><<<epi_blocks(g, ne), 256, 0, s>>>(U, V, Dl, HV, ne, k, g->d_scalars, pm2, skip);
+  PSPEC_CUDA(cudaGetLastError());
+  return PSPEC_OK;
+}
+
+pspec_status eval_fast(pspec_graph* g, const float* U, int k, double p, double* F_out, float* grad,
+                       double* parts, cudaStream_t s, bool keep_delta) {
+  const int64_t ne = g->n_owned * k;
+  float* Dl = grad;  // the edge kernel's Delta rows: in place over grad, or kept
+  if (keep_delta) {
+    PSPEC_TRY(ensure_delta_keep(g, (size_t)ne));
+    Dl = g->d_delta_keep;
+  }
+  EdgeLaunch L{U, nullptr, Dl, nullptr, p, k};
+  PSPEC_TRY(launch_eval_edges(g, L, s));
+  PSPEC_TRY(run_grad_epilogue(g, U, Dl, grad, k, p, s));
+  if (keep_delta)  // N[16], D[16] of this point, for the Hessian products that reuse its Delta
+    PSPEC_CUDA(cudaMemcpyAsync(g->d_scalars + kSlotKeep, g->d_scalars + kSlotN, sizeof(double) * 32,
+                               cudaMemcpyDeviceToDevice, s));
   if (F_out)
     PSPEC_CUDA(cudaMemcpyAsync(F_out, g->d_scalars + kSlotF, sizeof(double), cudaMemcpyDeviceToDevice, s));
   if (parts) {
@@ -163,7 +206,7 @@ pspec_status eval_fast(pspec_graph* g, const float* U, int k, double p, double* 
   return PSPEC_OK;
 }
 
-static pspec_status ensure_scratch(pspec_graph* g, size_t elems) {
+pspec_status ensure_scratch(pspec_graph* g, size_t elems) {
   if (g->scratch_elems >= elems) return PSPEC_OK;
   if (g->d_scratch) cudaFree(g->d_scratch);
   g->d_scratch = nullptr;
@@ -176,25 +219,25 @@ static pspec_status ensure_scratch(pspec_graph* g, size_t elems) {
 pspec_status hvp_edges_fast(pspec_graph* g, const float* U, const float* V, int k, double p, float* S,
                             cudaStream_t s, const int* skip, bool alg1) {
   PSPEC_TRY(ensure_scratch(g, (size_t)g->n * k));
-  EdgeLaunch L{U, V, S, g->d_scratch, (float)p, k, skip};
+  EdgeLaunch L{U, V, S, g->d_scratch, p, k, skip};
   L.alg1 = alg1;
   return launch_hvp_edges(g, L, s);
 }
 
 pspec_status hvp_fast(pspec_graph* g, const float* U, const float* V, int k, double p, float* HV,
-                      cudaStream_t s, const int* skip, bool alg1) {
-  const int64_t ne = g->n * k;
-  PSPEC_TRY(hvp_edges_fast(g, U, V, k, p, HV, s, skip, alg1));
-  const float pm2 = (float)p - 2.0f;
-  TimedScope timer(g, "hvp_epilogue", s);
-  if (k % 4 == 0)
-    hvp_epilogue<4><<<epi_blocks(g, ne / 4), 256, 0, s>>>(U, V, g->d_scratch, HV, ne, k, g->d_scalars, pm2, skip);
-  else if (k % 2 == 0)
-    hvp_epilogue<2><<<epi_blocks(g, ne / 2), 256, 0, s>>>(U, V, g->d_scratch, HV, ne, k, g->d_scalars, pm2, skip);
-  else
-    hvp_epilogue<1><<<epi_blocks(g, ne), 256, 0, s>>>(U, V, g->d_scratch, HV, ne, k, g->d_scalars, pm2, skip);
-  PSPEC_CUDA(cudaGetLastError());
-  return PSPEC_OK;
+                      cudaStream_t s, const int* skip, bool alg1, bool delta_kept) {
+  const float* Dl;
+  if (delta_kept) {  // Delta_p u, N and D from pspec_eval(PSPEC_KEEP_DELTA): the edge kernel skips them
+    EdgeLaunch L{U, V, HV, nullptr, p, k, skip};
+    L.alg1 = alg1;
+    L.keep_nd = g->d_scalars + kSlotKeep;
+    PSPEC_TRY(launch_hvp_edges(g, L, s));
+    Dl = g->d_delta_keep;
+  } else {
+    PSPEC_TRY(hvp_edges_fast(g, U, V, k, p, HV, s, skip, alg1));
+    Dl = g->d_scratch;
+  }
+  return run_hvp_epilogue(g, U, V, Dl, HV, k, p, s, skip);
 }
 
 // ------------------------------------------------------------- batches ---
@@ -345,7 +388,7 @@ static const int32_t* graph_task_of(pspec_graph* g, int k) {
 pspec_status eval_batched(pspec_graph* g, const float* U, int k, double p, double* F_out, float* grad,
                           double* parts, cudaStream_t s) {
   PSPEC_TRY(ensure_task_part(g, k));
-  EdgeLaunch L{U, nullptr, grad, nullptr, (float)p, k, nullptr, g->d_task_part};
+  EdgeLaunch L{U, nullptr, grad, nullptr, p, k, nullptr, g->d_task_part};
   PSPEC_TRY(launch_eval_edges(g, L, s));
   const int G = g->n_graphs;
   {
@@ -384,7 +427,7 @@ pspec_status hvp_batched(pspec_graph* g, const float* U, const float* V, int k, 
   const int64_t ne = g->n * k;
   PSPEC_TRY(ensure_scratch(g, (size_t)ne));
   PSPEC_TRY(ensure_task_part(g, k));
-  EdgeLaunch L{U, V, HV, g->d_scratch, (float)p, k, nullptr, g->d_task_part};
+  EdgeLaunch L{U, V, HV, g->d_scratch, p, k, nullptr, g->d_task_part};
   PSPEC_TRY(launch_hvp_edges(g, L, s));
   {
     TimedScope timer(g, "batch_reduce", s);
@@ -415,9 +458,13 @@ extern "C" pspec_status pspec_eval(pspec_graph* g, const void* U, int k, double 
                                    double* F_out, void* grad_out, double* parts_out, unsigned flags,
                                    void* stream) {
   PSPEC_TRY(check_common(g, k, p));
+  if (g->is_shard)
+    return set_error(PSPEC_ERR_INVALID_ARG, "a shard handle takes pspec_eval_partial / pspec_eval_finish");
   if (dtype != PSPEC_F32 && dtype != PSPEC_F64) return set_error(PSPEC_ERR_INVALID_ARG, "bad dtype");
   if (g->n_graphs != 1 && dtype != PSPEC_F32)
     return set_error(PSPEC_ERR_INVALID_ARG, "batched graphs run the FP32 path");
+  if ((flags & PSPEC_KEEP_DELTA) && (g->n_graphs != 1 || dtype != PSPEC_F32))
+    return set_error(PSPEC_ERR_INVALID_ARG, "PSPEC_KEEP_DELTA needs an FP32 call on a single graph");
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = (size_t)g->n * k * elem_size(dtype);
   const void* dU = U;
@@ -440,12 +487,21 @@ extern "C" pspec_status pspec_eval(pspec_graph* g, const void* U, int k, double 
     PSPEC_TRY(check_block(grad_out, k, dtype, "grad_out"));
     if (U == grad_out) return set_error(PSPEC_ERR_INVALID_ARG, "grad_out aliases U");
   }
+  const bool keep = (flags & PSPEC_KEEP_DELTA) != 0;
+  if (keep) g->keep_valid = false;  // until this call's rows are enqueued
   if (G > 1)
     PSPEC_TRY(eval_batched(g, (const float*)dU, k, p, dF, (float*)dG, dP, s));
   else if (dtype == PSPEC_F32)
-    PSPEC_TRY(eval_fast(g, (const float*)dU, k, p, dF, (float*)dG, dP, s));
+    PSPEC_TRY(eval_fast(g, (const float*)dU, k, p, dF, (float*)dG, dP, s, keep));
   else
     PSPEC_TRY(eval_plain64(g, (const double*)dU, k, p, dF, (double*)dG, dP, s));
+  if (keep) {
+    g->keep_valid = true;
+    g->keep_U = U;
+    g->keep_host = flags & PSPEC_HOST_PTRS;
+    g->keep_k = k;
+    g->keep_p = p;
+  }
   if (flags & PSPEC_HOST_PTRS) {
     PSPEC_CUDA(cudaMemcpyAsync(grad_out, dG, bytes, cudaMemcpyDeviceToHost, s));
     if (F_out) PSPEC_CUDA(cudaMemcpyAsync(F_out, dF, sizeof(double) * G, cudaMemcpyDeviceToHost, s));
@@ -459,9 +515,21 @@ extern "C" pspec_status pspec_eval(pspec_graph* g, const void* U, int k, double 
 extern "C" pspec_status pspec_hvp(pspec_graph* g, const void* U, const void* V, int k, double p,
                                   pspec_dtype dtype, void* HV_out, unsigned flags, void* stream) {
   PSPEC_TRY(check_common(g, k, p));
+  if (g->is_shard)
+    return set_error(PSPEC_ERR_INVALID_ARG, "a shard handle takes pspec_hvp_partial / pspec_hvp_finish");
   if (dtype != PSPEC_F32 && dtype != PSPEC_F64) return set_error(PSPEC_ERR_INVALID_ARG, "bad dtype");
   if (g->n_graphs != 1 && dtype != PSPEC_F32)
     return set_error(PSPEC_ERR_INVALID_ARG, "batched graphs run the FP32 path");
+  const bool kept = (flags & PSPEC_DELTA_KEPT) != 0;
+  if (kept) {
+    if (g->n_graphs != 1 || dtype != PSPEC_F32)
+      return set_error(PSPEC_ERR_INVALID_ARG, "PSPEC_DELTA_KEPT needs an FP32 call on a single graph");
+    if (!g->keep_valid || g->keep_U != U || g->keep_k != k || g->keep_p != p ||
+        g->keep_host != (flags & PSPEC_HOST_PTRS))
+      return set_error(PSPEC_ERR_INVALID_ARG,
+                       "PSPEC_DELTA_KEPT: no Delta_p u kept for this U pointer, k and p "
+                       "(call pspec_eval with PSPEC_KEEP_DELTA first)");
+  }
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = (size_t)g->n * k * elem_size(dtype);
   const void* dU = U;
@@ -487,7 +555,7 @@ extern "C" pspec_status pspec_hvp(pspec_graph* g, const void* U, const void* V, 
   if (g->n_graphs > 1)
     PSPEC_TRY(hvp_batched(g, (const float*)dU, (const float*)dV, k, p, (float*)dH, s, alg1));
   else if (dtype == PSPEC_F32)
-    PSPEC_TRY(hvp_fast(g, (const float*)dU, (const float*)dV, k, p, (float*)dH, s, nullptr, alg1));
+    PSPEC_TRY(hvp_fast(g, (const float*)dU, (const float*)dV, k, p, (float*)dH, s, nullptr, alg1, kept));
   else
     PSPEC_TRY(hvp_plain64(g, (const double*)dU, (const double*)dV, k, p, (double*)dH, s, alg1));
   if (flags & PSPEC_HOST_PTRS) {

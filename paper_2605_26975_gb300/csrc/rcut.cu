@@ -125,5 +125,6 @@ extern "C" pspec_status pspec_rcut(pspec_graph* g, const int32_t* labels, int n_
   if (!g || !labels || !rcut_out) return set_error(PSPEC_ERR_INVALID_ARG, "NULL argument");
   if (n_clusters < 1 || n_clusters > kRcMaxC) return set_error(PSPEC_ERR_INVALID_ARG, "n_clusters must be in [1, 1024]");
   if (g->n_graphs != 1) return set_error(PSPEC_ERR_INVALID_ARG, "pspec_rcut takes a single graph");
+  if (g->is_shard) return set_error(PSPEC_ERR_INVALID_ARG, "pspec_rcut takes a whole graph, not a shard");
   return rcut_impl(g, labels, n_clusters, rcut_out, (cudaStream_t)stream);
 }

@@ -512,6 +512,7 @@ extern "C" pspec_status pspec_solve(pspec_graph* g, int k, const double* p_sched
                                     void* stream) {
   if (!g) return set_error(PSPEC_ERR_INVALID_ARG, "graph is NULL");
   if (g->n_graphs != 1) return set_error(PSPEC_ERR_INVALID_ARG, "pspec_solve takes a single graph");
+  if (g->is_shard) return set_error(PSPEC_ERR_INVALID_ARG, "pspec_solve takes a whole graph, not a shard");
   if (k < 1 || k > kMaxK) return set_error(PSPEC_ERR_INVALID_ARG, "k must be in [1, 16]");
   if (k > g->n) return set_error(PSPEC_ERR_INVALID_ARG, "k exceeds n");
   pspec_solve_opts o;

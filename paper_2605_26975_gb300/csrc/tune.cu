@@ -29,7 +29,7 @@ static pspec_status tune_impl(pspec_graph* g, const float* U, const float* V, in
                               pspec_tune_report* rep, cudaStream_t s, float* G, float* H) {
   const int Q = q_of(k);
   const int qi = q_index(Q);
-  int occ = 0;  // resident blocks per SM of the HVP kernel at its register count
+  int occ = 0;  // resident blocks per SM of the direct HVP kernel at its register count
   PSPEC_TRY(edge_occupancy(k, true, &occ));
   std::vector<int> bps = {0};
   if (occ > 1) bps.push_back(occ - 1);
@@ -37,7 +37,7 @@ static pspec_status tune_impl(pspec_graph* g, const float* U, const float* V, in
   cudaEvent_t e0, e1;
   PSPEC_CUDA(cudaEventCreate(&e0));
   PSPEC_CUDA(cudaEventCreate(&e1));
-  int n = 0, best = -1;
+  int n = 0, best = -1, best_b = 0;
   double best_ms = 0.0;
   pspec_status st = PSPEC_OK;
   for (int L : Ls) {
@@ -60,6 +60,7 @@ static pspec_status tune_impl(pspec_graph* g, const float* U, const float* V, in
       rep->ms[n] = (double)ms / reps;
       if (best < 0 || rep->ms[n] < best_ms) {
         best = n;
+        best_b = b;
         best_ms = rep->ms[n];
       }
       ++n;
@@ -72,8 +73,9 @@ static pspec_status tune_impl(pspec_graph* g, const float* U, const float* V, in
   rep->chosen = best;
   free_tasks(g->tasks[qi]);
   if (best >= 0) {
+    // 0 = as many blocks as each kernel fits (the kernels of a shape differ)
     g->edges_per_lane[qi] = rep->edges_per_lane[best];
-    g->edge_blocks_per_sm[qi] = rep->blocks_per_sm[best];
+    g->edge_blocks_per_sm[qi] = best_b;
   } else {
     g->edges_per_lane[qi] = 0;
     g->edge_blocks_per_sm[qi] = 0;

@@ -128,3 +128,45 @@ def hvp_term_scale(oracle, g, U, V, p):
         r2 = (np.abs(gN) * aDv + np.abs(gD) * aNv + 2 * lam * np.abs(gD) * aDv) / D[l] ** 2
         out[:, l] = (s + diag) / D[l] + r2
     return out
+
+
+def check_eval(api, g, G, U, p):
+    """pspec_eval on U (FP32) against the oracle: F, N, D, and the gradient
+    per column and entry by entry."""
+    import torch
+    import oracle
+    Ud = torch.from_numpy(U).cuda()
+    F, grad, parts = G.eval(Ud, p, parts=True)
+    torch.cuda.synchronize()
+    assert G.status() == 0
+    U64 = U.astype(np.float64)
+    F_ref = oracle.objective(g, U64, p)
+    N, D = oracle.objective_parts(g, U64, p)
+    gr_ref = oracle.euclidean_grad(g, U64, p)
+    assert abs(F.item() - F_ref) <= TOL_F * abs(F_ref)
+    P = parts.cpu().numpy()
+    k = U.shape[1]
+    assert np.allclose(P[:k], N, rtol=TOL_F, atol=0)
+    assert np.allclose(P[k:], D, rtol=TOL_F, atol=0)
+    got = grad.cpu().numpy()
+    assert rel_col(got, gr_ref) <= TOL_GRAD
+    # entry by entry, against the magnitude of the entry's terms: a wrong
+    # value on a low-degree or small-|u| row cannot hide in a column norm
+    assert rel_elem(got, gr_ref, grad_term_scale(oracle, g, U64, p)) <= TOL_GRAD
+
+
+def check_hvp(api, g, G, U, V, p):
+    """pspec_hvp on U, V (FP32) against the oracle, per column and entry by
+    entry."""
+    import torch
+    import oracle
+    Ud = torch.from_numpy(U).cuda()
+    Vd = torch.from_numpy(V).cuda()
+    HV = G.hvp(Ud, Vd, p)
+    torch.cuda.synchronize()
+    assert G.status() == 0
+    U64, V64 = U.astype(np.float64), V.astype(np.float64)
+    ref = oracle.euclidean_hvp(g, U64, V64, p)
+    got = HV.cpu().numpy()
+    assert rel_col(got, ref) <= TOL_HVP
+    assert rel_elem(got, ref, hvp_term_scale(oracle, g, U64, V64, p)) <= TOL_HVP

@@ -63,38 +63,79 @@ def test_backward_matches_oracle_fp32(mods):
     assert torch.equal(hv, G.hvp(U.detach(), Vt, 1.4))
 
 
+def kink_free_direction(g, U64, V, h):
+    """V with its entries zeroed wherever a step of size h along it would carry
+    an edge difference u_i - u_j or a vertex value u_i across zero, where F is
+    not smooth (|t|^p); zeroing is repeated until no entry crosses, so central
+    differences of F along the result see a smooth function."""
+    rows = np.repeat(np.arange(g.n), np.diff(g.rowptr))
+    col = g.col.astype(np.int64)
+    V = V / np.linalg.norm(V)  # unit step; the margin 2 covers the renormalisation
+    for l in range(V.shape[1]):
+        u = np.ascontiguousarray(U64[:, l])
+        v = np.ascontiguousarray(V[:, l])
+        ad = np.abs(u[rows] - u[col])
+        while True:
+            # strict: an entry that does not move (zero step) cannot cross
+            bad = ad < 2.0 * h * np.abs(v[rows] - v[col])
+            badv = np.abs(u) < 2.0 * h * np.abs(v)
+            if not bad.any() and not badv.any():
+                break
+            v[rows[bad]] = 0.0
+            v[col[bad]] = 0.0
+            v[badv] = 0.0
+        V[:, l] = v
+    return V / np.linalg.norm(V)
+
+
 @pytest.mark.slow
-def test_dcsbm_autograd_central_differences(mods):
+def test_dcsbm_autograd_against_oracle(mods):
     """n = 1,000,000, 16 blocks, power-law degrees, k = 16, p = 1.3: the FP32
-    autograd gradient against central differences of F in FP64 (h = 1e-3, unit
-    direction) and the FP64 device gradient; the double backward against the
-    FP64 Hessian product."""
+    autograd gradient against the oracle's, entry by entry; its directional
+    derivative against Richardson-extrapolated central differences of the
+    oracle's F (h = 1e-3 and 5e-4, FP64) along a direction on which no edge
+    difference changes sign inside the stencil; the double backward against
+    the oracle's Hessian product on sampled rows (hubs included)."""
+    import oracle_rows as orw
+    from gpu_common import rel_elem
     api, ag = mods
     g = wl.make_graph("dcsbm")
     G = api.Graph.from_csr(g)
     k, p, h = 16, 1.3, 1e-3
     U0, _ = wl.make_blocks("dcsbm", g.n, k)
-    V0 = wl.gaussian_block(77, g.n, k, dtype=np.float64)
-    V0 /= np.linalg.norm(V0)
+    U64 = U0.astype(np.float64)
     U = torch.from_numpy(U0).cuda().requires_grad_(True)
     F = ag.p_objective(U, G, p)
     (gr,) = torch.autograd.grad(F, U, create_graph=True)
-    U64 = torch.from_numpy(U0.astype(np.float64)).cuda()
-    Vd = torch.from_numpy(V0).cuda()
-    Fp, _ = G.eval(U64 + h * Vd, p)
-    Fm, _ = G.eval(U64 - h * Vd, p)
-    fd = (Fp.item() - Fm.item()) / (2 * h)
-    dd = float((gr.double() * Vd).sum())
-    _, g64 = G.eval(U64, p)
-    dd64 = float((g64 * Vd).sum())
-    # the FP32 autograd derivative against the exact FP64 one
-    assert abs(dd - dd64) <= 1e-5 * abs(dd64)
-    assert rel_col(gr.detach().cpu().numpy(), g64.cpu().numpy()) <= 1e-5
-    # central differences: at p = 1.3 the few edges whose difference changes
-    # sign inside the +-h stencil (|d| < h |v_i - v_j|, ~1e-4 of the 16M
-    # entries) bend F like |t|^p, which bounds the stencil's agreement to ~1e-4
-    assert abs(dd64 - fd) <= 1e-3 * abs(fd)
     V32 = torch.from_numpy(wl.gaussian_block(78, g.n, k)).cuda()
     (hv,) = torch.autograd.grad(gr, U, grad_outputs=V32)
-    hv64 = G.hvp(U64, V32.double(), p)
-    assert rel_col(hv.cpu().numpy(), hv64.cpu().numpy()) <= 1e-4
+    torch.cuda.synchronize()
+    N, D = orw.oracle_N_D(g, U64, p)
+    assert abs(F.item() - np.sum(N / D)) <= 1e-5 * np.sum(N / D)
+    delta = orw.oracle_delta(g, U64, p)
+    gr_ref = orw.oracle_grad(g, U64, p, N, D, delta)
+    got = gr.detach().cpu().numpy()
+    assert rel_col(got, gr_ref) <= 1e-5
+    assert rel_elem(got, gr_ref, orw.grad_scale(g, U64, p, N, D)) <= 1e-5
+    # directional derivative against central differences of the oracle's F
+    Vd = kink_free_direction(g, U64, wl.gaussian_block(77, g.n, k, dtype=np.float64), h)
+
+    def F_oracle(X):
+        Nx, Dx = orw.oracle_N_D(g, X, p, rows_per_chunk=250_000)
+        return float(np.sum(Nx / Dx))
+
+    def central(step):
+        return (F_oracle(U64 + step * Vd) - F_oracle(U64 - step * Vd)) / (2 * step)
+
+    fd = (4 * central(h / 2) - central(h)) / 3  # Richardson: error O(h^4)
+    dd_ref = float(np.sum(gr_ref * Vd))
+    dd = float(np.sum(got.astype(np.float64) * Vd))
+    assert abs(dd_ref - fd) <= 1e-6 * abs(fd)  # the oracle's gradient and its F agree
+    assert abs(dd - fd) <= 1e-4 * abs(fd)
+    # double backward: the Hessian product on sampled rows
+    rng = np.random.default_rng(5)
+    deg = np.diff(g.rowptr)
+    rows = np.unique(np.concatenate([rng.choice(g.n, 300, replace=False),
+                                     np.argsort(deg, kind="stable")[-20:]]))
+    ref = orw.oracle_hvp_rows(g, U64, V32.cpu().numpy().astype(np.float64), p, rows, N, D, delta)
+    assert rel_col(hv.cpu().numpy()[rows], ref) <= 1e-4

@@ -7,8 +7,8 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_common import (TOL_F, TOL_F64, TOL_GRAD, TOL_HVP, grad_term_scale, hvp_term_scale,
-                        quantised_block, rel_col, rel_elem, small_graphs, tied_heavy_graph)
+from gpu_common import (TOL_F64, check_eval, check_hvp, quantised_block, rel_col, small_graphs,
+                        tied_heavy_graph)
 from paper_2605_26975_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -37,40 +37,6 @@ def blocks(n, k, seed):
     U = wl.orthonormal_block(seed, n, k, np.float32)
     V = wl.gaussian_block(seed + 1, n, k, dtype=np.float32)
     return U, V
-
-
-def check_eval(api, g, G, U, p):
-    Ud = torch.from_numpy(U).cuda()
-    F, grad, parts = G.eval(Ud, p, parts=True)
-    torch.cuda.synchronize()
-    assert G.status() == 0
-    U64 = U.astype(np.float64)
-    F_ref = oracle.objective(g, U64, p)
-    N, D = oracle.objective_parts(g, U64, p)
-    gr_ref = oracle.euclidean_grad(g, U64, p)
-    assert abs(F.item() - F_ref) <= TOL_F * abs(F_ref)
-    P = parts.cpu().numpy()
-    k = U.shape[1]
-    assert np.allclose(P[:k], N, rtol=TOL_F, atol=0)
-    assert np.allclose(P[k:], D, rtol=TOL_F, atol=0)
-    got = grad.cpu().numpy()
-    assert rel_col(got, gr_ref) <= TOL_GRAD
-    # entry by entry, against the magnitude of the entry's terms: a wrong
-    # value on a low-degree or small-|u| row cannot hide in a column norm
-    assert rel_elem(got, gr_ref, grad_term_scale(oracle, g, U64, p)) <= TOL_GRAD
-
-
-def check_hvp(api, g, G, U, V, p):
-    Ud = torch.from_numpy(U).cuda()
-    Vd = torch.from_numpy(V).cuda()
-    HV = G.hvp(Ud, Vd, p)
-    torch.cuda.synchronize()
-    assert G.status() == 0
-    U64, V64 = U.astype(np.float64), V.astype(np.float64)
-    ref = oracle.euclidean_hvp(g, U64, V64, p)
-    got = HV.cpu().numpy()
-    assert rel_col(got, ref) <= TOL_HVP
-    assert rel_elem(got, ref, hvp_term_scale(oracle, g, U64, V64, p)) <= TOL_HVP
 
 
 @pytest.mark.parametrize("name", ["sbm", "grid", "knn", "hubs", "isolated"])
@@ -136,6 +102,48 @@ def test_plain_fp64_path(api, graphs, k):
         assert abs(F.item() - oracle.objective(g, U64, p)) <= TOL_F64 * abs(F.item())
         assert rel_col(grad.cpu().numpy(), oracle.euclidean_grad(g, U64, p)) <= TOL_F64
         assert rel_col(HV.cpu().numpy(), oracle.euclidean_hvp(g, U64, V64, p)) <= 1e-10
+
+
+def test_kept_delta_reuse(api, graphs):
+    """pspec_eval(PSPEC_KEEP_DELTA) then pspec_hvp(PSPEC_DELTA_KEPT) at the same
+    U: the gradient is bit-identical to the plain call's, the Hessian product
+    matches the oracle (and the plain call within rounding), through device
+    and host pointers; a kept Delta for another U, k or p is refused."""
+    from paper_2605_26975_gb300 import _abi
+    g, G = graphs["hubs"]
+    U, V = blocks(g.n, 8, 61)
+    Ud, Vd = torch.from_numpy(U).cuda(), torch.from_numpy(V).cuda()
+    for p in (1.3, 2.0, 1.05):
+        F1, g1 = G.eval(Ud, p)
+        F2, g2 = G.eval(Ud, p, keep_delta=True)
+        h_plain = G.hvp(Ud, Vd, p)
+        h_kept = G.hvp(Ud, Vd, p, delta_kept=True)
+        torch.cuda.synchronize()
+        assert G.status() == 0
+        assert F1.item() == F2.item() and torch.equal(g1, g2)
+        ref = oracle.euclidean_hvp(g, U.astype(np.float64), V.astype(np.float64), p)
+        assert rel_col(h_kept.cpu().numpy(), ref) <= 1e-4
+        assert rel_col(h_kept.cpu().numpy(), h_plain.cpu().numpy().astype(np.float64)) <= 1e-5
+    # host pointers: the same kept rows through PSPEC_HOST_PTRS
+    Uh, Vh = torch.from_numpy(U).pin_memory(), torch.from_numpy(V).pin_memory()
+    gh, hh = torch.empty_like(Uh).pin_memory(), torch.empty_like(Uh).pin_memory()
+    G.eval_host(Uh, 1.3, gh, keep_delta=True)
+    G.hvp_host(Uh, Vh, 1.3, hh, delta_kept=True)
+    G.eval(Ud, 1.3, keep_delta=True)
+    hd = G.hvp(Ud, Vd, 1.3, delta_kept=True)
+    torch.cuda.synchronize()
+    assert torch.equal(hh, hd.cpu())
+    # refused: another p, another U pointer, another k, the host flag, FP64
+    with pytest.raises(_abi.PspecError):
+        G.hvp(Ud, Vd, 1.7, delta_kept=True)
+    with pytest.raises(_abi.PspecError):
+        G.hvp(Ud.clone(), Vd, 1.3, delta_kept=True)
+    with pytest.raises(_abi.PspecError):
+        G.hvp(Ud[:, :4].contiguous(), Vd[:, :4].contiguous(), 1.3, delta_kept=True)
+    with pytest.raises(_abi.PspecError):
+        G.hvp_host(Uh, Vh, 1.3, hh, delta_kept=True)  # the last KEEP was a device call
+    with pytest.raises(_abi.PspecError):
+        G.eval(Ud.double(), 1.3, keep_delta=True)
 
 
 def test_bit_reproducible(api, graphs):
