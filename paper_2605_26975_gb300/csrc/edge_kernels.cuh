@@ -163,13 +163,7 @@ struct AccBank<CPL, NQ, COMP, false> {
 // gathers' latency is hidden by that many warps.
 template <int K, int MODE>
 __host__ __device__ constexpr int edge_min_blocks() {
-  return K / q_of(K) <= 4 ? 4 : 1;
-}
-
-// Whether the direct kernel issues a task's first loads one task ahead (PF).
-template <int K, int MODE>
-__host__ __device__ constexpr bool edge_prefetch() {
-  return MODE == kModeHvpKept && K / q_of(K) <= 4;
+  return K / q_of(K) <= 4 ? ((MODE == kModeHvpKept && K >= 8) ? 5 : 4) : 1;
 }
 
 // task descriptor fields (see ensure_tasks)
@@ -355,7 +349,6 @@ template <int K, int MODE>
 __global__ void __launch_bounds__(kBlock, edge_min_blocks<K, MODE>()) edge_kernel(EdgeArgs a) {
   constexpr bool HVP = MODE != kModeEval;
   constexpr bool KEPT = MODE == kModeHvpKept;
-  constexpr bool PF = edge_prefetch<K, MODE>();
   constexpr int Q = q_of(K);
   constexpr int CPL = K / Q;
   constexpr int VW = vw_of(K);
@@ -382,49 +375,16 @@ __global__ void __launch_bounds__(kBlock, edge_min_blocks<K, MODE>()) edge_kerne
   Acc acc;
   acc.init(s_acc);
 
-  // With PF the loads a task starts with -- its descriptor, its row's vertex
-  // and its first entries -- are issued one task ahead (the descriptor two
-  // ahead), so a task's chain of dependent loads starts at its own row and
-  // neighbour rows.
-  int4 pf_task = make_int4(0, 0, 0, 0), pf_next = make_int4(0, 0, 0, 0);
-  int pf_row = 0;
-  int2 pf_e[UNR];
-  if constexpr (PF) {
-    if (gwarp < a.n_tasks) {
-      pf_task = __ldg(&a.tasks[gwarp]);
-      const LaneTask v = lane_task<Q>(pf_task, lane);
-      if (v.active) pf_row = __ldg(&a.perm[v.prow]);
-      if (v.n_my >= UNR) load_entries<UNR>(a.cw + v.start + v.slot, v.E, pf_e);
-    }
-    if (gwarp + nwarps < a.n_tasks) pf_next = __ldg(&a.tasks[gwarp + nwarps]);
-  }
-
   for (int t = gwarp; t < a.n_tasks; t += nwarps) {
-    const int4 task = PF ? pf_task : __ldg(&a.tasks[t]);
+    const int4 task = __ldg(&a.tasks[t]);
     const LaneTask lt = lane_task<Q>(task, lane);
     const bool hub = lt.hub;
     const int elog = lt.elog, E = lt.E, T = lt.T, slot = lt.slot, n_my = lt.n_my;
     const bool active = lt.active;
     const int2* cw = a.cw + lt.start + slot;  // this lane's entries: cw[j * E], j < n_my
     int2 nx[UNR];
-    int64_t row;
-    if constexpr (PF) {
-#pragma unroll
-      for (int u = 0; u < UNR; ++u) nx[u] = pf_e[u];
-      row = active ? (int64_t)pf_row : 0;
-      // the next task's first loads, and the descriptor of the one after it
-      const int tn = t + nwarps;
-      pf_task = pf_next;
-      if (tn < a.n_tasks) {
-        const LaneTask v = lane_task<Q>(pf_task, lane);
-        if (v.active) pf_row = __ldg(&a.perm[v.prow]);
-        if (v.n_my >= UNR) load_entries<UNR>(a.cw + v.start + v.slot, v.E, pf_e);
-      }
-      if (tn + nwarps < a.n_tasks) pf_next = __ldg(&a.tasks[tn + nwarps]);
-    } else {
-      if (n_my >= UNR) load_entries<UNR>(cw, E, nx);
-      row = active ? (int64_t)__ldg(&a.perm[lt.prow]) : 0;
-    }
+    if (n_my >= UNR) load_entries<UNR>(cw, E, nx);
+    const int64_t row = active ? (int64_t)__ldg(&a.perm[lt.prow]) : 0;
 
     float ui[CPL], vi[CPL], dsum[CPL], nsum[CPL], ssum[CPL];
 #pragma unroll
