@@ -47,9 +47,10 @@ STEP = "pspec_eval (F + grad, Delta_p u kept) + pspec_hvp at the same U (Delta_p
 STEP_PLAIN = "pspec_eval (F + grad) + pspec_hvp"
 L2_NOTE = "flushed (256 MB write) before every timed step"
 L2_FLUSH_BYTES = 256 << 20
+# the device code of the edge kernels: a profiles/ summary taken on other
+# sources gives no traffic figure
 KERNEL_SOURCES = ["paper_2605_26975_gb300/csrc/edge_kernels.cuh",
                   "paper_2605_26975_gb300/csrc/edge_staged.cuh",
-                  "paper_2605_26975_gb300/csrc/edge_launch.cuh",
                   "paper_2605_26975_gb300/csrc/common.cuh"]
 
 
@@ -67,6 +68,8 @@ def parse():
     ap.add_argument("--solve-gtol", type=float, default=None,
                     help="relative gradient tolerance of every stage (library default 1e-6)")
     ap.add_argument("--no-solve", action="store_true", help="same as --solve none")
+    ap.add_argument("--solve-perturbed", action="store_true",
+                    help="with --solve both: also the FP64 solve from U0 perturbed at FP32 rounding")
     ap.add_argument("--no-keep", action="store_true",
                     help="plain pspec_hvp (the HVP kernel writes Delta_p u again)")
     ap.add_argument("--no-cpu", action="store_true")
@@ -615,6 +618,7 @@ def main():
             solve["f64"] = run_solve(torch.from_numpy(pt.U.astype(np.float64)).cuda())
             solve["speedup"] = solve["f64"]["s"] / solve["f32"]["s"]
             solve["rcut_rel_diff"] = abs(solve["f32"]["rcut"] - solve["f64"]["rcut"]) / solve["f64"]["rcut"]
+        if args.solve == "both" and args.solve_perturbed:
             # the same FP64 solve from U0 perturbed at FP32's rounding level
             # (each entry times 1 + 2^-24 s, s = +-1 seeded): how far apart two
             # FP64 paths end from starting points as close as FP32 rounding

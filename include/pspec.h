@@ -172,13 +172,17 @@ pspec_status pspec_hvp(pspec_graph* g, const void* U, const void* V, int k, doub
  * d <= L*E, so L fixes how many rows a warp task holds, 32/(E*Q), and whether
  * the staged kernel -- for tasks short enough for its shared-memory buffers,
  * L <= 8 at k = 4, 8, 16 -- or the direct one runs) and the resident blocks per SM
- * (as many as each kernel fits, and one fewer than the direct kernel fits).  Each candidate runs one untimed eval + HVP and then `reps` timed
+ * (as many as each kernel fits, and one and two fewer than the direct HVP
+ * kernel fits).  Each candidate runs one untimed eval + HVP and then `reps` timed
  * ones on U, V (device, n x k row-major FP32); the fastest is kept on the
  * handle for every later FP32 call with this k's column split (it changes
  * the summation order of the per-column sums, within the stated tolerance,
  * and results stay bit-reproducible for a fixed shape).  The paper has no
  * counterpart; the shape is a property of the hardware.  Allocates two n x k
  * FP32 outputs for the duration of the call and synchronises `stream`.
+ * A single graph's candidates are timed on the pair a Newton step repeats
+ * (pspec_eval keeping Delta_p u, then pspec_hvp reusing it; a batch: the
+ * plain pair); the call drops whatever Delta_p u the handle kept.
  * report receives every candidate's mean eval + HVP time.  Errors:
  * INVALID_ARG (k, p, reps outside [1, 1000], NULL, misalignment), CUDA, OOM. */
 #define PSPEC_TUNE_MAX 16

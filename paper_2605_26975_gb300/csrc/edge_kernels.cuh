@@ -77,6 +77,9 @@ struct EdgeArgs {
   // evaluation's N[16], D[16] (the staged kernel then sums only sigma_N and
   // sigma_D); NULL otherwise
   const double* keep_nd;
+  // contiguous task ranges, warp w taking [warp_begin[w], warp_begin[w+1]);
+  // NULL: round-robin
+  const int32_t* warp_begin;
 };
 
 // What an edge kernel sums: the objective (N, D, Delta_p u), the Hessian
@@ -159,11 +162,12 @@ struct AccBank<CPL, NQ, COMP, false> {
 // Resident blocks per SM the kernel is compiled for: with lanes of at most
 // four columns the kernels fit four blocks of 256 threads (64 registers)
 // without spilling, and the Hessian product at a kept point (no |d|^p sum,
-// two column sums instead of four) fits five (48 registers) for k >= 8; the
+// two column sums instead of four) fits five (48 registers) for k = 8 (at
+// k = 16 that register budget made it slower than four blocks at 64); the
 // gathers' latency is hidden by that many warps.
-template <int K, int MODE>
+template <int K, int MODE, bool SPLIT>
 __host__ __device__ constexpr int edge_min_blocks() {
-  return K / q_of(K) <= 4 ? ((MODE == kModeHvpKept && K >= 8) ? 5 : 4) : 1;
+  return K / q_of(K) <= 4 ? ((MODE == kModeHvpKept && K >= 8 && K < 16 && !SPLIT) ? 5 : 4) : 1;
 }
 
 // task descriptor fields (see ensure_tasks)
@@ -345,8 +349,10 @@ __device__ __forceinline__ LaneTask lane_task(int4 task, int lane) {
   return v;
 }
 
-template <int K, int MODE>
-__global__ void __launch_bounds__(kBlock, edge_min_blocks<K, MODE>()) edge_kernel(EdgeArgs a) {
+// SPLIT: the warps take contiguous, cost-balanced task ranges (a.warp_begin)
+// instead of round-robin tasks
+template <int K, int MODE, bool SPLIT>
+__global__ void __launch_bounds__(kBlock, edge_min_blocks<K, MODE, SPLIT>()) edge_kernel(EdgeArgs a) {
   constexpr bool HVP = MODE != kModeEval;
   constexpr bool KEPT = MODE == kModeHvpKept;
   constexpr int Q = q_of(K);
@@ -375,7 +381,9 @@ __global__ void __launch_bounds__(kBlock, edge_min_blocks<K, MODE>()) edge_kerne
   Acc acc;
   acc.init(s_acc);
 
-  for (int t = gwarp; t < a.n_tasks; t += nwarps) {
+  const int t_first = SPLIT ? __ldg(&a.warp_begin[gwarp]) : gwarp;
+  const int t_end = SPLIT ? __ldg(&a.warp_begin[gwarp + 1]) : a.n_tasks;
+  for (int t = t_first; t < t_end; t += SPLIT ? 1 : nwarps) {
     const int4 task = __ldg(&a.tasks[t]);
     const LaneTask lt = lane_task<Q>(task, lane);
     const bool hub = lt.hub;

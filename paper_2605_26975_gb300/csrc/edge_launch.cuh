@@ -42,18 +42,41 @@ pspec_status launch_staged(pspec_graph* g, const EdgeArgs& a, int max_entries, i
   return PSPEC_OK;
 }
 
-template <int K, int MODE>
-pspec_status launch_direct(pspec_graph* g, const EdgeArgs& a, int64_t n_tasks, int want, cudaStream_t s) {
+// below this many tasks per warp the direct kernel takes contiguous,
+// cost-balanced ranges of the (degree-sorted) task list instead of
+// round-robin tasks, so the heavy tail is spread evenly; both are fixed
+// assignments, so results stay bit-reproducible
+constexpr int kSplitTasksPerWarp = 8;
+
+template <int K, int MODE, bool SPLIT>
+int direct_blocks(pspec_graph* g, int64_t n_tasks, int want) {
   // resident blocks at the kernel's register count, once per process
   static const int occ_direct = [] {
     int o = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, edge_kernel<K, MODE>, kBlock, 0) != cudaSuccess) o = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, edge_kernel<K, MODE, SPLIT>, kBlock, 0) != cudaSuccess)
+      o = 1;
     return std::max(o, 1);
   }();
   const int occ = env_blocks_per_sm(occ_direct);
-  int blocks = grid_blocks(g, want > 0 ? std::min(want, occ) : occ);
-  blocks = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (n_tasks + kWarps - 1) / kWarps));
-  edge_kernel<K, MODE><<<blocks, kBlock, 0, s>>>(a);
+  const int blocks = grid_blocks(g, want > 0 ? std::min(want, occ) : occ);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (n_tasks + kWarps - 1) / kWarps));
+}
+
+template <int K, int MODE>
+pspec_status launch_direct(pspec_graph* g, EdgeArgs a, TaskSet& ts, int want, cudaStream_t s) {
+  const int64_t n_tasks = ts.n_tasks;
+  const int rr_blocks = direct_blocks<K, MODE, false>(g, n_tasks, want);
+  a.warp_begin = nullptr;
+  if (n_tasks < (int64_t)kSplitTasksPerWarp * rr_blocks * kWarps) {
+    const int blocks = direct_blocks<K, MODE, true>(g, n_tasks, want);
+    PSPEC_TRY(ensure_split(ts, blocks * kWarps, s, &a.warp_begin));
+    if (a.warp_begin) {
+      edge_kernel<K, MODE, true><<<blocks, kBlock, 0, s>>>(a);
+      PSPEC_CUDA(cudaGetLastError());
+      return PSPEC_OK;
+    }
+  }
+  edge_kernel<K, MODE, false><<<rr_blocks, kBlock, 0, s>>>(a);
   PSPEC_CUDA(cudaGetLastError());
   return PSPEC_OK;
 }
@@ -62,7 +85,7 @@ template <int K, bool HVP>
 pspec_status launch_edges_k(pspec_graph* g, const EdgeLaunch& L, cudaStream_t s) {
   constexpr int Q = q_of(K);
   PSPEC_TRY(ensure_tasks(g, Q));
-  const TaskSet& ts = g->tasks[q_index(Q)];
+  TaskSet& ts = g->tasks[q_index(Q)];
   EdgeArgs a;
   a.cw = g->d_cw_s;
   a.perm = g->d_perm;
@@ -89,6 +112,7 @@ pspec_status launch_edges_k(pspec_graph* g, const EdgeLaunch& L, cudaStream_t s)
   a.task_part = L.task_part;
   a.alg1 = L.alg1 ? 1 : 0;
   a.keep_nd = L.keep_nd;
+  a.warp_begin = nullptr;
   const int want = g->edge_blocks_per_sm[q_index(Q)];
   TimedScope timer(g, HVP ? "hvp_edges" : "eval_edges", s);
   const int max_entries = ts.chunk_edges;  // 32 L / Q
@@ -97,15 +121,21 @@ pspec_status launch_edges_k(pspec_graph* g, const EdgeLaunch& L, cudaStream_t s)
     else if (L.keep_nd) return launch_staged<K, kModeHvpKept>(g, a, max_entries, want, s);
     else return launch_staged<K, kModeHvp>(g, a, max_entries, want, s);
   }
-  if constexpr (!HVP) return launch_direct<K, kModeEval>(g, a, ts.n_tasks, want, s);
-  else if (L.keep_nd) return launch_direct<K, kModeHvpKept>(g, a, ts.n_tasks, want, s);
-  else return launch_direct<K, kModeHvp>(g, a, ts.n_tasks, want, s);
+  if constexpr (!HVP) return launch_direct<K, kModeEval>(g, a, ts, want, s);
+  else if (L.keep_nd) return launch_direct<K, kModeHvpKept>(g, a, ts, want, s);
+  else return launch_direct<K, kModeHvp>(g, a, ts, want, s);
 }
 
+// resident blocks per SM of the direct kernel of a mode (the HVP one at a
+// kept point when `kept`)
 template <int K, bool HVP>
-pspec_status occupancy_k(int* blocks_per_sm) {
-  PSPEC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      blocks_per_sm, edge_kernel<K, HVP ? kModeHvp : kModeEval>, kBlock, 0));
+pspec_status occupancy_k(int* blocks_per_sm, bool kept) {
+  if (HVP && kept)
+    PSPEC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, edge_kernel<K, kModeHvpKept, false>,
+                                                             kBlock, 0));
+  else
+    PSPEC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        blocks_per_sm, edge_kernel<K, HVP ? kModeHvp : kModeEval, false>, kBlock, 0));
   return PSPEC_OK;
 }
 
@@ -116,5 +146,5 @@ pspec_status occupancy_k(int* blocks_per_sm) {
                                                         cudaStream_t);                      \
   template pspec_status pspec::launch_edges_k<K, true>(pspec_graph*, const pspec::EdgeLaunch&,  \
                                                        cudaStream_t);                      \
-  template pspec_status pspec::occupancy_k<K, false>(int*);                                 \
-  template pspec_status pspec::occupancy_k<K, true>(int*);
+  template pspec_status pspec::occupancy_k<K, false>(int*, bool);                           \
+  template pspec_status pspec::occupancy_k<K, true>(int*, bool);

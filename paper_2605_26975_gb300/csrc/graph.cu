@@ -84,6 +84,7 @@ pspec_status ensure_io(pspec_graph* g, size_t bytes) {
     g->h_pinned_bytes = bytes;
   }
   if (g->d_io_bytes < bytes) {
+    g->io_u_kept = false;
     if (g->d_io) cudaFree(g->d_io);
     g->d_io = nullptr;
     g->d_io_bytes = 0;
@@ -112,7 +113,36 @@ void free_tasks(TaskSet& ts) {
   cudaFree(ts.d_chunk_hub);
   cudaFree(ts.d_task_graph);
   cudaFree(ts.d_graph_task);
+  for (auto& sp : ts.splits) cudaFree(sp.second);
   ts = TaskSet();
+}
+
+pspec_status ensure_split(TaskSet& ts, int nwarps, cudaStream_t s, const int32_t** out) {
+  *out = nullptr;
+  for (const auto& sp : ts.splits)
+    if (sp.first == nwarps) {
+      *out = sp.second;
+      return PSPEC_OK;
+    }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  PSPEC_CUDA(cudaStreamIsCapturing(s, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return PSPEC_OK;  // no upload inside a capture
+  // warp w starts at the first task whose cost prefix reaches w/nwarps of the total
+  const std::vector<int64_t>& c = ts.h_cost;
+  const int64_t total = c.back();
+  std::vector<int32_t> wb(nwarps + 1);
+  for (int w = 0; w <= nwarps; ++w) {
+    const int64_t target = (int64_t)((__int128)total * w / nwarps);
+    wb[w] = (int32_t)(std::lower_bound(c.begin(), c.end(), target) - c.begin());
+  }
+  wb[nwarps] = (int32_t)ts.n_tasks;
+  int32_t* d = nullptr;
+  PSPEC_CUDA(cudaMalloc(&d, sizeof(int32_t) * (nwarps + 1)));
+  ts.splits.emplace_back(nwarps, d);
+  PSPEC_CUDA(cudaMemcpy(d, wb.data(), sizeof(int32_t) * (nwarps + 1), cudaMemcpyHostToDevice));
+  PSPEC_CUDA(cudaStreamSynchronize(cudaStreamLegacy));  // uploaded before any stream's kernel reads it
+  *out = d;
+  return PSPEC_OK;
 }
 
 pspec_status ensure_tasks(pspec_graph* g, int Q) {
@@ -132,6 +162,10 @@ pspec_status ensure_tasks(pspec_graph* g, int Q) {
   const int64_t n = g->n_owned;  // a shard's halo rows (sorted last) get no tasks
   std::vector<int4> tasks;
   tasks.reserve((size_t)(n / 8 + 16));
+  // a task's cost ~ the entries one lane walks plus a fixed part (descriptor,
+  // vertex terms, sums, stores), in entry units
+  constexpr int64_t kTaskCostFixed = 4;
+  std::vector<int64_t> cost(1, 0);
   std::vector<int32_t> hub_row, hub_first, hub_nchunk, chunk_hub;
   int n_chunks = 0;
   auto elog_of = [&](int64_t d) {
@@ -167,6 +201,7 @@ pspec_status ensure_tasks(pspec_graph* g, int Q) {
         tasks.push_back(make_int4((int)r, n_chunks + c,
                                   max_elog | (1 << 8) | ((c == 0 ? 1 : 0) << 9) | (int)(len << 10),
                                   (int)(rp[r] + (int64_t)c * chunk)));
+        cost.push_back(cost.back() + (len + max_slots - 1) / max_slots + kTaskCostFixed);
         task_graph.push_back((int32_t)gi);
         chunk_hub.push_back((int32_t)hub_row.size() - 1);
       }
@@ -179,12 +214,14 @@ pspec_status ensure_tasks(pspec_graph* g, int Q) {
     int nrows = 0;
     while (nrows < R && r + nrows < gend && rp[r + nrows + 1] - rp[r + nrows] == deg) ++nrows;
     tasks.push_back(make_int4((int)r, nrows | (int)(deg << 8), elog, (int)rp[r]));
+    cost.push_back(cost.back() + (deg + (1 << elog) - 1) / (1 << elog) + kTaskCostFixed);
     task_graph.push_back((int32_t)gi);
     r += nrows;
   }
   for (size_t q = gi + 1; q < graph_task.size(); ++q) graph_task[q] = (int32_t)tasks.size();
   ts.Q = Q;
   ts.L = L;
+  ts.h_cost = std::move(cost);
   ts.chunk_edges = chunk;
   ts.n_tasks = (int64_t)tasks.size();
   ts.n_hubs = (int)hub_row.size();

@@ -37,6 +37,11 @@ struct TaskSet {
   int32_t* d_chunk_hub = nullptr;   // [n_chunks] hub index of each chunk
   int32_t* d_task_graph = nullptr;  // [n_tasks] graph of each task (batches)
   int32_t* d_graph_task = nullptr;  // [G+1] first task of each graph (batches)
+  // splits of the task list into contiguous, equally costly warp ranges
+  // (launches with few tasks per warp): prefix sums of each task's
+  // estimated cost, and per warp count the uploaded first task of each warp
+  std::vector<int64_t> h_cost;                      // [n_tasks + 1]
+  std::vector<std::pair<int, int32_t*>> splits;     // (warps, device [warps + 1])
 };
 
 struct Timing {
@@ -114,6 +119,7 @@ struct pspec_graph {
   size_t h_pinned_bytes = 0;
   void* d_io = nullptr;
   size_t d_io_bytes = 0;
+  bool io_u_kept = false;  // d_io's first block holds U of the kept point (host-pointer calls)
   // solver workspace (allocated on first solve)
   void* d_solve = nullptr;
   size_t d_solve_bytes = 0;
@@ -163,6 +169,9 @@ struct TimedScope {
 
 // task sets and workspace
 pspec_status ensure_tasks(pspec_graph* g, int Q);
+// the contiguous cost-balanced split of ts for nwarps warps (*out = NULL when
+// it cannot be uploaded now, e.g. during a stream capture)
+pspec_status ensure_split(TaskSet& ts, int nwarps, cudaStream_t s, const int32_t** out);
 void free_tasks(TaskSet& ts);
 inline int q_index(int Q) { return Q == 1 ? 0 : Q == 2 ? 1 : 2; }
 pspec_status ensure_io(pspec_graph* g, size_t bytes);
@@ -185,7 +194,7 @@ struct EdgeLaunch {
   bool alg1 = false;          // HVP: Algorithm 1's form (no rank-two terms)
   const double* keep_nd = nullptr;  // HVP at a kept point: its N[16], D[16]
 };
-pspec_status edge_occupancy(int k, bool hvp, int* blocks_per_sm);
+pspec_status edge_occupancy(int k, bool hvp, int* blocks_per_sm, bool kept = false);
 pspec_status launch_eval_edges(pspec_graph* g, const EdgeLaunch& a, cudaStream_t s);
 pspec_status launch_hvp_edges(pspec_graph* g, const EdgeLaunch& a, cudaStream_t s);
 
@@ -196,11 +205,20 @@ pspec_status hvp_plain64(pspec_graph* g, const double* U, const double* V, int k
                          double* HV, cudaStream_t s, bool alg1 = false);
 
 // FP32 fast path, device pointers only
+// keep_delta: Delta_p u of U into keep_rows (n x k) and N, D into keep_nd
+// (32 doubles), by default the handle's own kept point; delta_kept: the
+// Hessian product at a point kept that way (the same buffers)
 pspec_status eval_fast(pspec_graph* g, const float* U, int k, double p, double* F_out,
-                       float* grad, double* parts, cudaStream_t s, bool keep_delta = false);
+                       float* grad, double* parts, cudaStream_t s, bool keep_delta = false,
+                       float* keep_rows = nullptr, double* keep_nd = nullptr);
 pspec_status hvp_fast(pspec_graph* g, const float* U, const float* V, int k, double p, float* HV,
                       cudaStream_t s, const int* skip = nullptr, bool alg1 = false,
-                      bool delta_kept = false);
+                      bool delta_kept = false, const float* keep_rows = nullptr,
+                      const double* keep_nd = nullptr);
+// the edge kernel of a Hessian product at a kept point alone (sparse part into S)
+pspec_status hvp_kept_edges(pspec_graph* g, const float* U, const float* V, int k, double p, float* S,
+                            const double* keep_nd, cudaStream_t s, const int* skip = nullptr,
+                            bool alg1 = false);
 // the epilogues over the handle's n_owned rows: grad from the Delta rows Dl
 // (in place when Dl == grad), HV over the sparse part S held in HV; the
 // coefficients come from d_scalars

@@ -29,13 +29,13 @@ static pspec_status dispatch_edges(pspec_graph* g, const EdgeLaunch& L, cudaStre
 }
 
 template <int K, bool HVP>
-pspec_status occupancy_k(int* blocks_per_sm);
+pspec_status occupancy_k(int* blocks_per_sm, bool kept);
 
-pspec_status edge_occupancy(int k, bool hvp, int* blocks_per_sm) {
+pspec_status edge_occupancy(int k, bool hvp, int* blocks_per_sm, bool kept) {
   switch (k) {
 #define CASE(K) \
   case K:       \
-    return hvp ? occupancy_k<K, true>(blocks_per_sm) : occupancy_k<K, false>(blocks_per_sm);
+    return hvp ? occupancy_k<K, true>(blocks_per_sm, kept) : occupancy_k<K, false>(blocks_per_sm, kept);
     CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
     CASE(9) CASE(10) CASE(11) CASE(12) CASE(13) CASE(14) CASE(15) CASE(16)
 #undef CASE
@@ -184,19 +184,20 @@ pspec_status run_hvp_epilogue(pspec_graph* g, const float* U, const float* V, co
 }
 
 pspec_status eval_fast(pspec_graph* g, const float* U, int k, double p, double* F_out, float* grad,
-                       double* parts, cudaStream_t s, bool keep_delta) {
+                       double* parts, cudaStream_t s, bool keep_delta, float* keep_rows, double* keep_nd) {
   const int64_t ne = g->n_owned * k;
   float* Dl = grad;  // the edge kernel's Delta rows: in place over grad, or kept
-  if (keep_delta) {
+  if (keep_delta && !keep_rows) {  // the handle's own kept point (PSPEC_KEEP_DELTA)
     PSPEC_TRY(ensure_delta_keep(g, (size_t)ne));
-    Dl = g->d_delta_keep;
+    keep_rows = g->d_delta_keep;
+    keep_nd = g->d_scalars + kSlotKeep;
   }
+  if (keep_delta) Dl = keep_rows;
   EdgeLaunch L{U, nullptr, Dl, nullptr, p, k};
   PSPEC_TRY(launch_eval_edges(g, L, s));
   PSPEC_TRY(run_grad_epilogue(g, U, Dl, grad, k, p, s));
   if (keep_delta)  // N[16], D[16] of this point, for the Hessian products that reuse its Delta
-    PSPEC_CUDA(cudaMemcpyAsync(g->d_scalars + kSlotKeep, g->d_scalars + kSlotN, sizeof(double) * 32,
-                               cudaMemcpyDeviceToDevice, s));
+    PSPEC_CUDA(cudaMemcpyAsync(keep_nd, g->d_scalars + kSlotN, sizeof(double) * 32, cudaMemcpyDeviceToDevice, s));
   if (F_out)
     PSPEC_CUDA(cudaMemcpyAsync(F_out, g->d_scalars + kSlotF, sizeof(double), cudaMemcpyDeviceToDevice, s));
   if (parts) {
@@ -224,15 +225,25 @@ pspec_status hvp_edges_fast(pspec_graph* g, const float* U, const float* V, int 
   return launch_hvp_edges(g, L, s);
 }
 
+pspec_status hvp_kept_edges(pspec_graph* g, const float* U, const float* V, int k, double p, float* S,
+                            const double* keep_nd, cudaStream_t s, const int* skip, bool alg1) {
+  EdgeLaunch L{U, V, S, nullptr, p, k, skip};
+  L.alg1 = alg1;
+  L.keep_nd = keep_nd;
+  return launch_hvp_edges(g, L, s);
+}
+
 pspec_status hvp_fast(pspec_graph* g, const float* U, const float* V, int k, double p, float* HV,
-                      cudaStream_t s, const int* skip, bool alg1, bool delta_kept) {
+                      cudaStream_t s, const int* skip, bool alg1, bool delta_kept, const float* keep_rows,
+                      const double* keep_nd) {
   const float* Dl;
-  if (delta_kept) {  // Delta_p u, N and D from pspec_eval(PSPEC_KEEP_DELTA): the edge kernel skips them
-    EdgeLaunch L{U, V, HV, nullptr, p, k, skip};
-    L.alg1 = alg1;
-    L.keep_nd = g->d_scalars + kSlotKeep;
-    PSPEC_TRY(launch_hvp_edges(g, L, s));
-    Dl = g->d_delta_keep;
+  if (delta_kept) {  // Delta_p u, N and D of the evaluation at U: the edge kernel skips them
+    if (!keep_rows) {  // the handle's own kept point (PSPEC_KEEP_DELTA)
+      keep_rows = g->d_delta_keep;
+      keep_nd = g->d_scalars + kSlotKeep;
+    }
+    PSPEC_TRY(hvp_kept_edges(g, U, V, k, p, HV, keep_nd, s, skip, alg1));
+    Dl = keep_rows;
   } else {
     PSPEC_TRY(hvp_edges_fast(g, U, V, k, p, HV, s, skip, alg1));
     Dl = g->d_scratch;
@@ -475,7 +486,13 @@ extern "C" pspec_status pspec_eval(pspec_graph* g, const void* U, int k, double 
   if (flags & PSPEC_HOST_PTRS) {
     if (!U || !grad_out) return set_error(PSPEC_ERR_INVALID_ARG, "U or grad_out is NULL");
     const size_t ab = align_up(bytes);
-    PSPEC_TRY(ensure_io(g, 2 * ab + 256 + 8 * (size_t)G * (1 + 2 * kMaxK)));
+    // with PSPEC_KEEP_DELTA the staging area is sized for the Hessian
+    // products that follow (U, V, HV), so U's device copy stays where they
+    // look for it
+    size_t need = 2 * ab + 256 + 8 * (size_t)G * (1 + 2 * kMaxK);
+    if (flags & PSPEC_KEEP_DELTA) need = std::max(need, 3 * ab);
+    PSPEC_TRY(ensure_io(g, need));
+    g->io_u_kept = false;
     char* base = (char*)g->d_io;
     dU = base;
     dG = base + ab;
@@ -497,6 +514,7 @@ extern "C" pspec_status pspec_eval(pspec_graph* g, const void* U, int k, double 
     PSPEC_TRY(eval_plain64(g, (const double*)dU, k, p, dF, (double*)dG, dP, s));
   if (keep) {
     g->keep_valid = true;
+    g->io_u_kept = (flags & PSPEC_HOST_PTRS) != 0;  // the staged U is the kept point's
     g->keep_U = U;
     g->keep_host = flags & PSPEC_HOST_PTRS;
     g->keep_k = k;
@@ -543,7 +561,11 @@ extern "C" pspec_status pspec_hvp(pspec_graph* g, const void* U, const void* V, 
     dU = base;
     dV = base + ab;
     dH = base + 2 * ab;
-    PSPEC_CUDA(cudaMemcpyAsync((void*)dU, U, bytes, cudaMemcpyHostToDevice, s));
+    // at the kept point U's device copy is still staged (and unchanged, as
+    // PSPEC_DELTA_KEPT promises), unless another host-pointer call used the area
+    if (!(kept && g->io_u_kept))
+      PSPEC_CUDA(cudaMemcpyAsync((void*)dU, U, bytes, cudaMemcpyHostToDevice, s));
+    g->io_u_kept = kept;
     PSPEC_CUDA(cudaMemcpyAsync((void*)dV, V, bytes, cudaMemcpyHostToDevice, s));
   } else {
     PSPEC_TRY(check_block(U, k, dtype, "U"));

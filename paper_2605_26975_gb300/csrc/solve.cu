@@ -36,6 +36,10 @@ namespace {
 template <typename T>
 struct SolveWork {
   T *U, *Unew, *egrad, *egrad_new, *rg, *rg_new, *eta, *Heta, *r, *delta, *He, *Hd, *tmp;
+  // Delta_p u and N, D of the iterate and of the trial point (FP32: the
+  // Hessian products of truncated CG reuse the iterate's; they swap with it)
+  T *dk, *dk_new;
+  double *nd, *nd_new;
   double *M, *Mnew, *G, *Gram, *Rinv, *dots, *gdot, *F;
   TcgState* st;
   int* bad;
@@ -58,7 +62,7 @@ pspec_status carve(pspec_graph* g, int k, SolveWork<T>* w) {
   const int groups = (maxb + kGroup - 1) / kGroup;
   const size_t red = sizeof(double) * 256 * (size_t)(maxb + groups);
   const size_t small = 4096 * sizeof(double);
-  const size_t need = 13 * vec + 2 * red + small;
+  const size_t need = 15 * vec + 2 * red + small;
   if (g->d_solve_bytes < need) {
     if (g->d_solve) cudaFree(g->d_solve);
     g->d_solve = nullptr;
@@ -67,8 +71,8 @@ pspec_status carve(pspec_graph* g, int k, SolveWork<T>* w) {
     g->d_solve_bytes = need;
   }
   char* p = (char*)g->d_solve;
-  T** vecs[13] = {&w->U, &w->Unew, &w->egrad, &w->egrad_new, &w->rg, &w->rg_new, &w->eta,
-                  &w->Heta, &w->r, &w->delta, &w->He, &w->Hd, &w->tmp};
+  T** vecs[15] = {&w->U, &w->Unew, &w->egrad, &w->egrad_new, &w->rg, &w->rg_new, &w->eta,
+                  &w->Heta, &w->r, &w->delta, &w->He, &w->Hd, &w->tmp, &w->dk, &w->dk_new};
   for (auto v : vecs) {
     *v = (T*)p;
     p += vec;
@@ -87,6 +91,8 @@ pspec_status carve(pspec_graph* g, int k, SolveWork<T>* w) {
   w->bad = (int*)(sm + 1100);
   w->Mnew = sm + 1280;
   w->gdot = sm + 1536;
+  w->nd = sm + 1600;
+  w->nd_new = sm + 1664;
   w->gr.counters = g->d_counters;
   return PSPEC_OK;
 }
@@ -139,17 +145,20 @@ struct Solver {
   SolveWork<T> w;
   int64_t evals = 0, hvps = 0;
 
-  pspec_status eval(const T* U, double p, T* grad) {
+  // F and the gradient at U; the FP32 path also keeps U's Delta_p u, N, D
+  // in (dk, nd) for the Hessian products at U
+  pspec_status eval(const T* U, double p, T* grad, T* dk, double* nd) {
     ++evals;
     if constexpr (sizeof(T) == 4)
-      return eval_fast(g, U, k, p, w.F, grad, nullptr, s);
+      return eval_fast(g, U, k, p, w.F, grad, nullptr, s, true, dk, nd);
     else
       return eval_plain64(g, U, k, p, w.F, grad, nullptr, s);
   }
   bool alg1 = false;  // Algorithm 1's Hessian form instead of the exact one
+  // the Hessian product at the iterate U (whose Delta_p u, N, D are w.dk, w.nd)
   pspec_status hvp(const T* U, const T* V, double p, T* out, const int* skip) {
     if constexpr (sizeof(T) == 4)
-      return hvp_fast(g, U, V, k, p, out, s, skip, alg1);
+      return hvp_fast(g, U, V, k, p, out, s, skip, alg1, true, w.dk, w.nd);
     else
       return hvp_plain64(g, U, V, k, p, out, s, alg1);
   }
@@ -158,9 +167,9 @@ struct Solver {
   pspec_status hvp_gram(const T* U, const T* V, double p, T* Hv, double* Gm, const int* done) {
     if constexpr (sizeof(T) == 4) {
       if (k % 4 == 0) {
-        PSPEC_TRY(hvp_edges_fast(g, U, V, k, p, Hv, s, done, alg1));
+        PSPEC_TRY(hvp_kept_edges(g, U, V, k, p, Hv, w.nd, s, done, alg1));
         TimedScope timer(g, "hvp_epi_gram", s);
-        hvp_epi_gram_kernel<<<w.tblocks, kSolveBlock, 0, s>>>(U, V, g->d_scratch, Hv, n, k, g->d_scalars,
+        hvp_epi_gram_kernel<<<w.tblocks, kSolveBlock, 0, s>>>(U, V, w.dk, Hv, n, k, g->d_scalars,
                                                               (float)p - 2.0f, Gm, w.gr, done);
         PSPEC_CUDA(cudaGetLastError());
         return PSPEC_OK;
@@ -296,7 +305,7 @@ static pspec_status solve_impl(pspec_graph* g, int k, const double* sched, int n
   for (int ip = 0; ip < n_p; ++ip) {
     const double p = sched[ip];
     double f = 0.0, gnorm = 0.0;
-    PSPEC_TRY(S.eval(w.U, p, w.egrad));
+    PSPEC_TRY(S.eval(w.U, p, w.egrad, w.dk, w.nd));
     PSPEC_TRY(S.riemannian_grad(w.U, w.egrad, w.M, w.rg, w.gdot));
     PSPEC_TRY(S.fetch(false));
     PSPEC_TRY(status_error(S.rec->status));
@@ -366,7 +375,7 @@ static pspec_status solve_impl(pspec_graph* g, int k, const double* sched, int n
       // ---- trial point, model decrease, ratio
       PSPEC_TRY(S.combine(w.tmp, w.U, 1.0, w.eta, 1.0, nullptr, nullptr, nullptr, nullptr));
       PSPEC_TRY(S.qf(w.tmp, w.Unew));
-      PSPEC_TRY(S.eval(w.Unew, p, w.egrad_new));
+      PSPEC_TRY(S.eval(w.Unew, p, w.egrad_new, w.dk_new, w.nd_new));
       DotPairs<T> dp{};
       dp.x[0] = w.rg;
       dp.y[0] = w.eta;
@@ -394,9 +403,11 @@ static pspec_status solve_impl(pspec_graph* g, int k, const double* sched, int n
       if (o.verbose)
         std::fprintf(stderr, "pspec p=%.3f it=%d f=%.10e |g|=%.3e tcg=%d(%d) rho=%.3f Delta=%.3e %s\n", p,
                      outer, f, gnorm, hs.j, hs.reason, rho, Delta, accept ? "acc" : "rej");
-      if (accept) {  // the iterate, its gradient and U^T grad move together
+      if (accept) {  // the iterate, its gradient, U^T grad and Delta_p u move together
         std::swap(w.U, w.Unew);
         std::swap(w.egrad, w.egrad_new);
+        std::swap(w.dk, w.dk_new);
+        std::swap(w.nd, w.nd_new);
         std::swap(w.M, w.Mnew);
         std::swap(w.rg, w.rg_new);
         f = f_new;

@@ -15,24 +15,30 @@
 
 namespace pspec {
 
+// The pair a Newton step repeats: the evaluation at U, keeping Delta_p u, and
+// a Hessian product at U reusing it (a batch has no kept form: its plain pair).
 static pspec_status run_pair(pspec_graph* g, const float* U, const float* V, int k, double p, float* G,
                              float* H, cudaStream_t s) {
   if (g->n_graphs > 1) {
     PSPEC_TRY(eval_batched(g, U, k, p, nullptr, G, nullptr, s));
     return hvp_batched(g, U, V, k, p, H, s);
   }
-  PSPEC_TRY(eval_fast(g, U, k, p, nullptr, G, nullptr, s));
-  return hvp_fast(g, U, V, k, p, H, s, nullptr);
+  PSPEC_TRY(eval_fast(g, U, k, p, nullptr, G, nullptr, s, /*keep_delta=*/true));
+  return hvp_fast(g, U, V, k, p, H, s, nullptr, false, /*delta_kept=*/true);
 }
 
 static pspec_status tune_impl(pspec_graph* g, const float* U, const float* V, int k, double p, int reps,
                               pspec_tune_report* rep, cudaStream_t s, float* G, float* H) {
+  g->keep_valid = false;  // the timed evaluations overwrite the kept Delta_p u
   const int Q = q_of(k);
   const int qi = q_index(Q);
-  int occ = 0;  // resident blocks per SM of the direct HVP kernel at its register count
-  PSPEC_TRY(edge_occupancy(k, true, &occ));
+  // resident blocks per SM of the direct HVP kernel the pair runs (kept
+  // form for a single graph): that many (0 = each kernel as many as it
+  // fits), one and two fewer
+  int occ = 0;
+  PSPEC_TRY(edge_occupancy(k, true, &occ, g->n_graphs == 1));
   std::vector<int> bps = {0};
-  if (occ > 1) bps.push_back(occ - 1);
+  for (int b = occ - 1; b >= std::max(1, occ - 2); --b) bps.push_back(b);
   const int Ls[] = {Q, 2 * Q, 4 * Q, 8 * Q, 16 * Q};
   cudaEvent_t e0, e1;
   PSPEC_CUDA(cudaEventCreate(&e0));

@@ -133,7 +133,17 @@ def test_kept_delta_reuse(api, graphs):
     hd = G.hvp(Ud, Vd, 1.3, delta_kept=True)
     torch.cuda.synchronize()
     assert torch.equal(hh, hd.cpu())
+    # the kept host-pointer HVP reuses the staged copy of U; a host-pointer
+    # call with another U in between must not leak into it
+    U2h = torch.from_numpy(blocks(g.n, 8, 62)[0]).pin_memory()
+    G.eval_host(Uh, 1.3, gh, keep_delta=True)
+    G.hvp_host(Uh, Vh, 1.3, hh, delta_kept=True)
+    G.eval_host(U2h, 1.3, torch.empty_like(gh).pin_memory())  # stages U2, keeps nothing new
+    h2 = torch.empty_like(hh).pin_memory()
+    G.hvp_host(Uh, Vh, 1.3, h2, delta_kept=True)  # Uh's kept record still stands
+    assert torch.equal(h2, hd.cpu()) and torch.equal(hh, hd.cpu())
     # refused: another p, another U pointer, another k, the host flag, FP64
+    G.eval(Ud, 1.3, keep_delta=True)  # the last kept point: a device-pointer call
     with pytest.raises(_abi.PspecError):
         G.hvp(Ud, Vd, 1.7, delta_kept=True)
     with pytest.raises(_abi.PspecError):
@@ -141,7 +151,7 @@ def test_kept_delta_reuse(api, graphs):
     with pytest.raises(_abi.PspecError):
         G.hvp(Ud[:, :4].contiguous(), Vd[:, :4].contiguous(), 1.3, delta_kept=True)
     with pytest.raises(_abi.PspecError):
-        G.hvp_host(Uh, Vh, 1.3, hh, delta_kept=True)  # the last KEEP was a device call
+        G.hvp_host(Uh, Vh, 1.3, hh, delta_kept=True)  # kept by a device-pointer call
     with pytest.raises(_abi.PspecError):
         G.eval(Ud.double(), 1.3, keep_delta=True)
 
