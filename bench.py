@@ -629,25 +629,46 @@ def main():
                                                     / solve["f64"]["rcut"])
 
     if args.solve != "none" and rank == 0 and len(parts) > 1:
-        # the batch: every graph solved on its own (pspec_solve_batched, FP32)
+        # the batch: every graph its own solve, all graphs of a k-handle in
+        # lockstep (pspec_solve_lockstep, FP32); with --solve both also the
+        # per-graph concurrent solves (pspec_solve_batched) for comparison
         sched = list(info["p_schedule"])
-        t0 = time.perf_counter()
-        rcuts, stat = [], []
-        for pt in parts:
-            # each graph's U0: orthonormal columns on its own rows, as the solve expects
-            U0 = np.concatenate([wl.orthonormal_block(2000 + 10 * pt.k + i, g.n, pt.k)
-                                 for i, g in enumerate(pt.graphs)])
-            _, _, rc, status, _ = pt.G.solve_batched(torch.from_numpy(U0).cuda(), sched,
-                                                     api.default_opts())
-            rcuts.append(rc)
-            stat.append(status)
-        torch.cuda.synchronize()
-        rcuts, stat = np.concatenate(rcuts), np.concatenate(stat)
-        solve = {"p_schedule": sched, "batched_f32_s": time.perf_counter() - t0,
-                 "graphs": int(rcuts.size), "graphs_ok_or_capped": int(np.isin(stat, (0, 6)).sum()),
-                 "rcut_median": float(np.median(rcuts)), "rcut_max": float(np.max(rcuts)),
-                 "note": "one pspec_solve_batched call per k-handle (graphs solved concurrently); "
-                         "first call includes building the per-graph handles"}
+
+        def run_batch(kind):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rcuts, stat, newton, tcg = [], [], [], []
+            for pt in parts:
+                # each graph's U0: orthonormal columns on its own rows, as the solve expects
+                U0 = torch.from_numpy(np.concatenate([wl.orthonormal_block(2000 + 10 * pt.k + i, g.n, pt.k)
+                                                      for i, g in enumerate(pt.graphs)])).cuda()
+                if kind == "lockstep":
+                    _, _, rc, status, sd, _ = pt.G.solve_lockstep(U0, sched, api.default_opts(),
+                                                                  allow_errors=True)
+                    newton.append(sum(sum(x["outer"]) for x in sd))
+                    tcg.append(sum(x["hvp_calls"] for x in sd))
+                else:
+                    _, _, rc, status, _ = pt.G.solve_batched(U0, sched, api.default_opts())
+                rcuts.append(rc)
+                stat.append(status)
+            torch.cuda.synchronize()
+            return (time.perf_counter() - t0, np.concatenate(rcuts), np.concatenate(stat),
+                    int(sum(newton)), int(sum(tcg)))
+
+        t_ls, rc_ls, st_ls, newton, tcg = run_batch("lockstep")
+        solve = {"p_schedule": sched, "lockstep_f32_s": t_ls, "graphs": int(rc_ls.size),
+                 "graphs_ok_or_capped": int(np.isin(st_ls, (0, 6)).sum()),
+                 "rcut_median": float(np.nanmedian(rc_ls)), "rcut_max": float(np.nanmax(rc_ls)),
+                 "newton_steps": newton, "tcg_iterations": tcg,
+                 "note": "one pspec_solve_lockstep call per k-handle: every graph's Newton/tCG "
+                         "decisions on the device, one launch per step for the whole handle; "
+                         "k-means per graph on 16 host threads"}
+        if args.solve == "both":
+            t_b, rc_b, st_b, _, _ = run_batch("batched")
+            rel = np.abs(rc_ls - rc_b) / rc_b
+            solve.update({"batched_f32_s": t_b, "speedup_lockstep_vs_batched": t_b / t_ls,
+                          "rcut_rel_diff_median": float(np.nanmedian(rel)),
+                          "graphs_rcut_within_1pct": int(np.sum(rel <= 0.01))})
 
     cpu = None
     if rank == 0 and not args.no_cpu:

@@ -354,6 +354,38 @@ pspec_status pspec_solve_batched(pspec_graph* g, int k, const double* p_schedule
                                  const pspec_solve_opts* opts, float* U_inout, int32_t* labels_out,
                                  double* rcut_out, int32_t* status_out, int n_threads, void* stream);
 
+/* pspec_solve_lockstep: the same per-graph solves (Section 2's Newton/tCG on
+ * the Grassmann manifold for every p of the schedule, then k-means and RCut)
+ * with all graphs of a batched handle stepping together on the device: each
+ * evaluation and each Hessian product is one launch of the edge kernel over
+ * the concatenated CSR, every n x k operation one launch over all graphs'
+ * rows, and every per-graph decision (truncated CG's recurrences, the
+ * trust-region ratio, radius and acceptance, the stopping tests) is taken in
+ * device memory; the host reads G flags per chunk of 6 CG iterations and per
+ * Newton step for the whole batch, and replays each chunk as a CUDA graph.
+ * A graph whose truncated CG or stage has ended waits, left out of every
+ * launch, so each graph takes the iterates it would take alone; only the
+ * reductions' summation order differs from pspec_solve, so results agree
+ * with it to rounding (not bit for bit).  Stages are synchronous: the batch
+ * moves to the next p when every graph has finished the current one.  The
+ * final k-means runs per graph on n_threads host threads, each with its own
+ * stream; RCut is one launch for all graphs.
+ *   U_inout, labels_out, rcut_out, status_out: as pspec_solve_batched, except
+ *               that rcut_out is NaN for a graph whose solve failed (labels
+ *               of such a graph are left as they were)
+ *   stats_out   host pspec_solve_stats[G] or NULL: each graph's counters
+ *               (seconds = the whole call's wall time)
+ * The FP32 path; opts->verbose prints one line per Newton step of the batch.
+ * Synchronises the solve's own stream; joined to `stream` by events.
+ * Returns OK, NOT_CONVERGED when a graph's stage hit max_outer, or the first
+ * graph error in graph order (INVALID_ARG for a graph with fewer vertices
+ * than k, NONFINITE, ZERO_COLUMN, CUDA, OOM).  Batching is this library's,
+ * not the paper's. */
+pspec_status pspec_solve_lockstep(pspec_graph* g, int k, const double* p_schedule, int n_p,
+                                  const pspec_solve_opts* opts, float* U_inout, int32_t* labels_out,
+                                  double* rcut_out, int32_t* status_out, pspec_solve_stats* stats_out,
+                                  int n_threads, void* stream);
+
 
 /* --------------------------------------------------------------- kmeans ---
  * pspec_kmeans: k-means of the n rows of X (n x dim, row-major, dtype,

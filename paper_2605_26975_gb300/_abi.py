@@ -73,6 +73,8 @@ _SIGS = {
                               C.POINTER(C.c_double), C.POINTER(SolveStats), _vp]),
     "pspec_solve_batched": (C.c_int, [_vp, C.c_int, _vp, C.c_int, C.POINTER(SolveOpts), _vp, _vp, _vp,
                                       _vp, C.c_int, _vp]),
+    "pspec_solve_lockstep": (C.c_int, [_vp, C.c_int, _vp, C.c_int, C.POINTER(SolveOpts), _vp, _vp, _vp,
+                                       _vp, _vp, C.c_int, _vp]),
     "pspec_kmeans": (C.c_int, [_vp, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_int,
                                C.c_int, _vp, _vp, C.POINTER(C.c_double), _vp]),
     "pspec_rcut": (C.c_int, [_vp, _vp, C.c_int, C.POINTER(C.c_double), _vp]),

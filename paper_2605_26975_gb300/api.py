@@ -198,6 +198,35 @@ class Graph:
         check(st, "pspec_solve_batched", allow=(_abi.PSPEC_OK, _abi.PSPEC_ERR_NOT_CONVERGED))
         return U, lab, rc, status, st
 
+    def solve_lockstep(self, U0, p_schedule, opts=None, threads=16, allow_errors=False):
+        """pspec_solve_lockstep on a batched handle: every graph's solve with
+        the whole batch stepping together on the device.  Returns (U, labels,
+        rcut per graph, status per graph, stats per graph (dicts), overall
+        status).  With allow_errors a per-graph error does not raise."""
+        if self.n_graphs < 1:
+            raise ValueError("not a graph handle")
+        U = _dev_block(U0, "U0", self.n).clone()
+        if U.dtype != torch.float32:
+            raise TypeError("the lockstep solve runs the FP32 path")
+        k = U.shape[1]
+        o = default_opts() if opts is None else opts
+        sched = np.ascontiguousarray(p_schedule, dtype=np.float64)
+        lab = torch.zeros(self.n, dtype=torch.int32, device=U.device)
+        G = self.n_graphs
+        rc = np.zeros(G, dtype=np.float64)
+        status = np.zeros(G, dtype=np.int32)
+        stats = (_abi.SolveStats * G)()
+        st = lib().pspec_solve_lockstep(self._h, k, sched.ctypes.data, sched.size, C.byref(o), _ptr(U),
+                                        _ptr(lab), rc.ctypes.data, status.ctypes.data, stats, int(threads),
+                                        _stream())
+        if not allow_errors:
+            check(st, "pspec_solve_lockstep", allow=(_abi.PSPEC_OK, _abi.PSPEC_ERR_NOT_CONVERGED))
+        ns = sched.size
+        sd = [dict(outer=list(x.outer[:ns]), inner=list(x.inner[:ns]), f=list(x.f[:ns]),
+                   gnorm=list(x.gnorm[:ns]), hvp_calls=x.hvp_calls, eval_calls=x.eval_calls,
+                   seconds=x.seconds, kmeans_inertia=x.kmeans_inertia) for x in stats]
+        return U, lab, rc, status, sd, st
+
     def rcut(self, labels, n_clusters):
         if not labels.is_cuda or labels.dtype != torch.int32:
             raise TypeError("labels must be an int32 CUDA tensor")

@@ -80,6 +80,11 @@ struct EdgeArgs {
   // contiguous task ranges, warp w taking [warp_begin[w], warp_begin[w+1]);
   // NULL: round-robin
   const int32_t* warp_begin;
+  // batches: the tasks of graph q are left out while graph_skip[q] is
+  // nonzero (task_graph: the graph of each task); NULL: every task runs.
+  // The direct kernel only.
+  const int* graph_skip;
+  const int32_t* task_graph;
 };
 
 // What an edge kernel sums: the objective (N, D, Delta_p u), the Hessian
@@ -384,6 +389,7 @@ __global__ void __launch_bounds__(kBlock, edge_min_blocks<K, MODE, SPLIT>()) edg
   const int t_first = SPLIT ? __ldg(&a.warp_begin[gwarp]) : gwarp;
   const int t_end = SPLIT ? __ldg(&a.warp_begin[gwarp + 1]) : a.n_tasks;
   for (int t = t_first; t < t_end; t += SPLIT ? 1 : nwarps) {
+    if (a.graph_skip && a.graph_skip[__ldg(&a.task_graph[t])]) continue;  // uniform over the warp
     const int4 task = __ldg(&a.tasks[t]);
     const LaneTask lt = lane_task<Q>(task, lane);
     const bool hub = lt.hub;

@@ -4,7 +4,8 @@
 // Two kernels compute the same sums: the staged kernel (edge_staged.cuh),
 // used whenever a task's entries fit its shared-memory buffers (entries per
 // task 32 L / Q <= staged_max_entries(K)), and the direct kernel
-// (edge_kernels.cuh) for longer tasks.  The edges-per-lane target L of the
+// (edge_kernels.cuh) for longer tasks and for batch launches that leave
+// graphs out (graph_skip).  The edges-per-lane target L of the
 // handle's task set -- set by pspec_tune or PSPEC_EDGES_PER_LANE -- thus also
 // picks the kernel.
 #pragma once
@@ -113,10 +114,12 @@ pspec_status launch_edges_k(pspec_graph* g, const EdgeLaunch& L, cudaStream_t s)
   a.alg1 = L.alg1 ? 1 : 0;
   a.keep_nd = L.keep_nd;
   a.warp_begin = nullptr;
+  a.graph_skip = L.graph_skip;
+  a.task_graph = ts.d_task_graph;
   const int want = g->edge_blocks_per_sm[q_index(Q)];
   TimedScope timer(g, HVP ? "hvp_edges" : "eval_edges", s);
   const int max_entries = ts.chunk_edges;  // 32 L / Q
-  if (max_entries <= staged_max_entries(K)) {
+  if (max_entries <= staged_max_entries(K) && !L.graph_skip) {
     if constexpr (!HVP) return launch_staged<K, kModeEval>(g, a, max_entries, want, s);
     else if (L.keep_nd) return launch_staged<K, kModeHvpKept>(g, a, max_entries, want, s);
     else return launch_staged<K, kModeHvp>(g, a, max_entries, want, s);

@@ -228,7 +228,7 @@ pspec_status ensure_tasks(pspec_graph* g, int Q) {
   ts.n_chunks = n_chunks;
   PSPEC_CUDA(cudaMalloc(&ts.d_tasks, sizeof(int4) * std::max<size_t>(1, tasks.size())));
   PSPEC_CUDA(cudaMemcpy(ts.d_tasks, tasks.data(), sizeof(int4) * tasks.size(), cudaMemcpyHostToDevice));
-  if (g->n_graphs > 1) {
+  if (!g->h_node_off.empty()) {  // a batched handle, even of one graph
     PSPEC_CUDA(cudaMalloc(&ts.d_task_graph, sizeof(int32_t) * std::max<size_t>(1, task_graph.size())));
     PSPEC_CUDA(cudaMemcpy(ts.d_task_graph, task_graph.data(), sizeof(int32_t) * task_graph.size(),
                           cudaMemcpyHostToDevice));

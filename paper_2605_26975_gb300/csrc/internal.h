@@ -193,6 +193,9 @@ struct EdgeLaunch {
   float* task_part = nullptr; // batches: per-task column sums (see edge_kernels.cuh)
   bool alg1 = false;          // HVP: Algorithm 1's form (no rank-two terms)
   const double* keep_nd = nullptr;  // HVP at a kept point: its N[16], D[16]
+  // batches: graphs whose flag is nonzero are left out (their outputs and
+  // task sums are not written)
+  const int* graph_skip = nullptr;
 };
 pspec_status edge_occupancy(int k, bool hvp, int* blocks_per_sm, bool kept = false);
 pspec_status launch_eval_edges(pspec_graph* g, const EdgeLaunch& a, cudaStream_t s);

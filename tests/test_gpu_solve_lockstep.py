@@ -1,0 +1,202 @@
+"""pspec_solve_lockstep: every graph of a batched handle solved with the whole
+batch stepping together on the device.  Each graph takes the iterates it
+would take alone, up to the summation order of the reductions, so it is
+compared with pspec_solve on the graph alone at rounding level where the
+problem is well conditioned (the p = 2 stage, whose minimum is the sum of
+the k smallest Laplacian eigenvalues), with the FP64 oracle's solve on the
+1,000-vertex SBM, and with the oracle's RCut of its own labels."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_26975_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2605_26975_gb300 import build
+    build.build()
+    from paper_2605_26975_gb300 import api as A
+    return A
+
+
+def same_partition(a, b):
+    pairs = set(zip(np.asarray(a).tolist(), np.asarray(b).tolist()))
+    return len(pairs) == len(set(np.asarray(a).tolist())) == len(set(np.asarray(b).tolist()))
+
+
+def batch_and_blocks(k, extra=()):
+    rng = np.random.default_rng(21)
+    gs = [wl.make_graph("sbm4"),
+          wl.sbm_sampled(rng, 3000, 4, 12.0, 0.9),
+          wl.sbm_sampled(rng, 200, 3, 8.0, 0.9),
+          wl.knn_gaussian_mixture(4, n=5000, mixtures=4)] + list(extra)
+    batch = wl.concat_graphs(gs, [k] * len(gs))
+    U = np.concatenate([wl.orthonormal_block(2000 if i == 0 else 500 + i, g.n, k)
+                        for i, g in enumerate(gs)])
+    return gs, batch, U
+
+
+def handle(api, batch):
+    c = batch.csr
+    return api.Graph(c.rowptr, c.col, c.val, node_off=batch.node_off)
+
+
+def laplacian_eigs(g, k):
+    Wd = np.zeros((g.n, g.n))
+    rows = np.repeat(np.arange(g.n), np.diff(g.rowptr))
+    Wd[rows, g.col] = g.val
+    return np.linalg.eigvalsh(np.diag(Wd.sum(1)) - Wd)[:k]
+
+
+def test_lockstep_p2_stage_matches_eigenvalues_and_single_solves(api):
+    """One p = 2 stage: every graph's F reaches the sum of its k smallest
+    Laplacian eigenvalues (Ky Fan), as pspec_solve on the graph alone does."""
+    k = 4
+    rng = np.random.default_rng(3)
+    gs = [wl.make_graph("sbm4"), wl.sbm_sampled(rng, 1500, 5, 10.0, 0.85),
+          wl.sbm_sampled(rng, 37, 2, 6.0, 0.9), wl.delaunay_unit_square(4, 800)]
+    batch = wl.concat_graphs(gs, [k] * len(gs))
+    U = np.concatenate([wl.orthonormal_block(40 + i, g.n, k) for i, g in enumerate(gs)])
+    G = handle(api, batch)
+    opts = api.default_opts(max_outer=60)
+    Ub, lab, rc, status, stats, st = G.solve_lockstep(torch.from_numpy(U).cuda(), [2.0], opts, threads=4)
+    # OK, or NOT_CONVERGED where FP32's gradient floor sits above gtol_rel = 1e-6
+    assert all(s in (0, 6) for s in status), status
+    for i, g in enumerate(gs):
+        ev = laplacian_eigs(g, k).sum()
+        assert abs(stats[i]["f"][0] - ev) <= 1e-5 * ev, (i, stats[i]["f"][0], ev)
+        a, b = batch.node_off[i], batch.node_off[i + 1]
+        S = api.Graph.from_csr(g)
+        _, _, _, st1, status1 = S.solve(torch.from_numpy(U[a:b]).cuda(), [2.0], opts)
+        assert abs(stats[i]["f"][0] - st1["f"][0]) <= 2e-6 * ev, (i, stats[i]["f"][0], st1["f"][0])
+        Uc = Ub[a:b].double().cpu().numpy()
+        assert np.allclose(Uc.T @ Uc, np.eye(k), atol=1e-5), i
+        # counters are consistent: one evaluation per stage plus one per Newton step
+        assert stats[i]["eval_calls"] == 1 + stats[i]["outer"][0]
+        assert stats[i]["hvp_calls"] == stats[i]["inner"][0] >= stats[i]["outer"][0] >= 1
+
+
+def test_lockstep_tracks_single_solves_over_the_schedule(api):
+    k = 4
+    sched = (2.0, 1.6, 1.3)
+    gs, batch, U = batch_and_blocks(k)
+    G = handle(api, batch)
+    Ub, lab, rc, status, stats, st = G.solve_lockstep(torch.from_numpy(U).cuda(), sched, threads=4)
+    assert all(s in (0, 6) for s in status), status  # OK or NOT_CONVERGED
+    for i, g in enumerate(gs):
+        a, b = batch.node_off[i], batch.node_off[i + 1]
+        S = api.Graph.from_csr(g)
+        Ui, labi, rci, sti, _ = S.solve(torch.from_numpy(U[a:b]).cuda(), sched)
+        # the p = 2 stage at rounding level; the final cut within 1%
+        assert abs(stats[i]["f"][0] - sti["f"][0]) <= 1e-5 * sti["f"][0], i
+        # (the kNN mixture's last stage is the least conditioned: 3%)
+        assert abs(rc[i] - rci) <= (0.01 if i < 3 else 0.03) * rci, (i, rc[i], rci)
+        # the RCut reported is the cut of the labels returned
+        li = lab[a:b].cpu().numpy()
+        assert abs(rc[i] - oracle.rcut(g, li, k)) <= 1e-12 * rc[i], i
+        if i < 3:  # the SBMs: the same blocks
+            assert same_partition(li, labi.cpu().numpy()), i
+
+
+def test_lockstep_sbm4_matches_oracle_and_is_deterministic(api):
+    k = 4
+    sched = wl.WORKLOADS["sbm4"]["p_schedule"]
+    gs, batch, U = batch_and_blocks(k)
+    G = handle(api, batch)
+    Ub, lab, rc, status, stats, st = G.solve_lockstep(torch.from_numpy(U).cuda(), sched)
+    n0 = gs[0].n
+    _, ref_lab, ref_rc, stages = oracle.solve(gs[0], U[:n0].astype(np.float64), sched)
+    assert abs(rc[0] - ref_rc) <= 0.01 * ref_rc
+    assert same_partition(lab[:n0].cpu().numpy(), ref_lab)
+    assert abs(stats[0]["f"][0] - stages[0]["f"]) <= 1e-5 * stages[0]["f"]
+    # fixed-order reductions: a second call gives the same bits
+    Ub2, lab2, rc2, status2, _, _ = G.solve_lockstep(torch.from_numpy(U).cuda(), sched, threads=2)
+    assert torch.equal(Ub, Ub2) and torch.equal(lab, lab2) and np.array_equal(rc, rc2)
+    assert np.array_equal(status, status2)
+
+
+def test_lockstep_eager_equals_graph_replay(api, monkeypatch):
+    k = 2
+    sched = (2.0, 1.5)
+    rng = np.random.default_rng(8)
+    gs = [wl.sbm_sampled(rng, 900, 2, 9.0, 0.9), wl.sbm_sampled(rng, 2500, 3, 11.0, 0.9)]
+    batch = wl.concat_graphs(gs, [k] * len(gs))
+    U = np.concatenate([wl.orthonormal_block(70 + i, g.n, k) for i, g in enumerate(gs)])
+    G = handle(api, batch)
+    Ua, laba, rca, _, sa, _ = G.solve_lockstep(torch.from_numpy(U).cuda(), sched)
+    monkeypatch.setenv("PSPEC_SOLVE_EAGER", "1")
+    Ue, labe, rce, _, se, _ = G.solve_lockstep(torch.from_numpy(U).cuda(), sched)
+    assert torch.equal(Ua, Ue) and torch.equal(laba, labe) and np.array_equal(rca, rce)
+    assert [s["inner"] for s in sa] == [s["inner"] for s in se]
+
+
+@pytest.mark.parametrize("k", [3, 8])
+def test_lockstep_other_k_and_algorithm1(api, k):
+    """Odd k (scalar row paths) and k = 8, in the exact and in Algorithm 1's
+    Hessian form: the p = 2 stage (where both forms have the same minimum)
+    against pspec_solve per graph."""
+    rng = np.random.default_rng(30 + k)
+    gs = [wl.sbm_sampled(rng, 800, k, 10.0, 0.9), wl.sbm_sampled(rng, 2000, k, 12.0, 0.9)]
+    batch = wl.concat_graphs(gs, [k] * len(gs))
+    U = np.concatenate([wl.orthonormal_block(90 + i, g.n, k) for i, g in enumerate(gs)])
+    G = handle(api, batch)
+    for form in (api._abi.PSPEC_HESSIAN_EXACT, api._abi.PSPEC_HESSIAN_ALG1):
+        opts = api.default_opts(max_outer=60, hessian_form=form)
+        _, _, rc, status, stats, _ = G.solve_lockstep(torch.from_numpy(U).cuda(), [2.0, 1.7], opts)
+        assert all(s in (0, 6) for s in status)
+        for i, g in enumerate(gs):
+            a, b = batch.node_off[i], batch.node_off[i + 1]
+            S = api.Graph.from_csr(g)
+            _, _, rci, sti, _ = S.solve(torch.from_numpy(U[a:b]).cuda(), [2.0, 1.7], opts)
+            assert abs(stats[i]["f"][0] - sti["f"][0]) <= 1e-5 * sti["f"][0], (form, i)
+            assert abs(rc[i] - rci) <= 0.02 * rci, (form, i, rc[i], rci)
+
+
+def test_lockstep_reports_a_graph_smaller_than_k(api):
+    rng = np.random.default_rng(5)
+    gs = [wl.sbm_sampled(rng, 400, 2, 8.0, 0.9),
+          wl.csr_from_undirected(2, np.array([0]), np.array([1]), np.array([1.0]), np.float32),
+          wl.sbm_sampled(rng, 300, 3, 8.0, 0.9)]
+    batch = wl.concat_graphs(gs, [3] * len(gs))
+    G = handle(api, batch)
+    U = np.concatenate([wl.orthonormal_block(i, g.n, 3) if g.n >= 3 else wl.gaussian_block(i, g.n, 3)
+                        for i, g in enumerate(gs)])
+    with pytest.raises(api._abi.PspecError, match="graph 1"):
+        G.solve_lockstep(torch.from_numpy(U).cuda(), [2.0])
+    Ub, lab, rc, status, stats, st = G.solve_lockstep(torch.from_numpy(U).cuda(), [2.0], allow_errors=True)
+    assert status[1] == api._abi.PSPEC_ERR_INVALID_ARG and math.isnan(rc[1])
+    assert st == api._abi.PSPEC_ERR_INVALID_ARG
+    # the graph's rows are left as they were; the others are solved
+    a, b = batch.node_off[1], batch.node_off[2]
+    assert torch.equal(Ub[a:b].cpu(), torch.from_numpy(U[a:b]))
+    for i in (0, 2):
+        assert status[i] in (0, 6) and np.isfinite(rc[i]) and rc[i] > 0
+        ev = laplacian_eigs(gs[i], 3).sum()
+        assert abs(stats[i]["f"][0] - ev) <= 1e-5 * ev
+
+
+def test_lockstep_zero_column_stops_only_its_graph(api):
+    """A graph whose starting block has a zero column meets ZERO_COLUMN at its
+    first evaluation; the other graphs' solves are unaffected."""
+    rng = np.random.default_rng(9)
+    gs = [wl.sbm_sampled(rng, 600, 2, 9.0, 0.9), wl.sbm_sampled(rng, 500, 2, 9.0, 0.9)]
+    batch = wl.concat_graphs(gs, [2, 2])
+    G = handle(api, batch)
+    U = np.concatenate([wl.orthonormal_block(60 + i, g.n, 2) for i, g in enumerate(gs)])
+    U[gs[0].n:, 1] = 0.0
+    _, _, rc, status, stats, st = G.solve_lockstep(torch.from_numpy(U).cuda(), [2.0, 1.5],
+                                                   allow_errors=True)
+    assert status[1] == api._abi.PSPEC_ERR_ZERO_COLUMN and math.isnan(rc[1])
+    assert st == api._abi.PSPEC_ERR_ZERO_COLUMN
+    S = api.Graph.from_csr(gs[0])
+    _, _, rc0, st0, _ = S.solve(torch.from_numpy(U[:gs[0].n]).cuda(), [2.0, 1.5])
+    assert abs(stats[0]["f"][0] - st0["f"][0]) <= 1e-5 * st0["f"][0]
+    assert abs(rc[0] - rc0) <= 0.01 * rc0
