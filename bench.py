@@ -634,23 +634,30 @@ def main():
         # per-graph concurrent solves (pspec_solve_batched) for comparison
         sched = list(info["p_schedule"])
 
+        # each graph's U0: orthonormal columns on its own rows, as the solve expects
+        U0s = [torch.from_numpy(np.concatenate([wl.orthonormal_block(2000 + 10 * pt.k + i, g.n, pt.k)
+                                                for i, g in enumerate(pt.graphs)])).cuda() for pt in parts]
+
         def run_batch(kind):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            rcuts, stat, newton, tcg = [], [], [], []
-            for pt in parts:
-                # each graph's U0: orthonormal columns on its own rows, as the solve expects
-                U0 = torch.from_numpy(np.concatenate([wl.orthonormal_block(2000 + 10 * pt.k + i, g.n, pt.k)
-                                                      for i, g in enumerate(pt.graphs)])).cuda()
-                if kind == "lockstep":
-                    _, _, rc, status, sd, _ = pt.G.solve_lockstep(U0, sched, api.default_opts(),
-                                                                  allow_errors=True)
-                    newton.append(sum(sum(x["outer"]) for x in sd))
-                    tcg.append(sum(x["hvp_calls"] for x in sd))
-                else:
+            if kind == "lockstep":
+                # the k-handles concurrently, each on its own solve stream
+                from concurrent.futures import ThreadPoolExecutor
+                with ThreadPoolExecutor(len(parts)) as ex:
+                    outs = list(ex.map(lambda a: a[0].G.solve_lockstep(a[1], sched, api.default_opts(),
+                                                                       allow_errors=True),
+                                       zip(parts, U0s)))
+                rcuts = [o[2] for o in outs]
+                stat = [o[3] for o in outs]
+                newton = [sum(sum(x["outer"]) for x in o[4]) for o in outs]
+                tcg = [sum(x["hvp_calls"] for x in o[4]) for o in outs]
+            else:
+                rcuts, stat, newton, tcg = [], [], [], []
+                for pt, U0 in zip(parts, U0s):
                     _, _, rc, status, _ = pt.G.solve_batched(U0, sched, api.default_opts())
-                rcuts.append(rc)
-                stat.append(status)
+                    rcuts.append(rc)
+                    stat.append(status)
             torch.cuda.synchronize()
             return (time.perf_counter() - t0, np.concatenate(rcuts), np.concatenate(stat),
                     int(sum(newton)), int(sum(tcg)))
@@ -660,9 +667,9 @@ def main():
                  "graphs_ok_or_capped": int(np.isin(st_ls, (0, 6)).sum()),
                  "rcut_median": float(np.nanmedian(rc_ls)), "rcut_max": float(np.nanmax(rc_ls)),
                  "newton_steps": newton, "tcg_iterations": tcg,
-                 "note": "one pspec_solve_lockstep call per k-handle: every graph's Newton/tCG "
-                         "decisions on the device, one launch per step for the whole handle; "
-                         "k-means per graph on 16 host threads"}
+                 "note": "one pspec_solve_lockstep call per k-handle, the three handles on host "
+                         "threads: every graph's Newton/tCG decisions on the device, one launch per "
+                         "step for the whole handle; k-means per graph on 16 host threads"}
         if args.solve == "both":
             t_b, rc_b, st_b, _, _ = run_batch("batched")
             rel = np.abs(rc_ls - rc_b) / rc_b

@@ -99,9 +99,6 @@ struct LsOpts {
   int max_outer, max_inner;
 };
 
-// A tile: graph x, first row y, rows z (<= kLsTile).
-__device__ __forceinline__ int4 ls_tile(const int4* tiles) { return __ldg(&tiles[blockIdx.x]); }
-
 // Block sum of ND per-thread float-float values in a fixed order (warp
 // trees, then warps in order); out (shared, ND doubles) is valid after the
 // call in every thread.
@@ -199,8 +196,18 @@ __global__ void __launch_bounds__(256) ls_reduce_kernel(const float* __restrict_
   const int t0 = graph_task[b], t1 = graph_task[b + 1];
   Kahan acc;
   acc.init();
-  if (jj < parts)
-    for (int t = t0 + jj; t < t1; t += parts) acc.add(__ldg(&part[(size_t)t * NV + v]));
+  if (jj < parts) {
+    // eight tasks' loads in flight at a time, added in task order
+    int t = t0 + jj;
+    for (; t + 7 * parts < t1; t += 8 * parts) {
+      float x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) x[u] = __ldg(&part[(size_t)(t + u * parts) * NV + v]);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc.add(x[u]);
+    }
+    for (; t < t1; t += parts) acc.add(__ldg(&part[(size_t)t * NV + v]));
+  }
   s_part[threadIdx.x] = kahan_to_ff(acc);
   __syncthreads();
   if (threadIdx.x < NV) {
@@ -245,396 +252,79 @@ __global__ void __launch_bounds__(256) ls_reduce_kernel(const float* __restrict_
   }
 }
 
-// Sum of every graph's tile partials (nv values per tile), a warp per graph,
-// tiles in order, into sc[graph][off..off+nv).
-__global__ void __launch_bounds__(256) ls_fin_kernel(const double* __restrict__ part, int PS,
-                                                     const int32_t* __restrict__ graph_tile, int G, int nv,
-                                                     const int* skip, double* sc, int stride, int off) {
-  const int b = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (b >= G || skip[b]) return;
-  const int t0 = graph_tile[b], t1 = graph_tile[b + 1];
-  for (int v = lane; v < nv; v += 32) {
-    double s = 0.0;
-    for (int t = t0; t < t1; ++t) s += part[(size_t)t * PS + v];
-    sc[(size_t)b * stride + off + v] = s;
-  }
+// ------------------------------------------------- per-graph completion ---
+// The row kernels walk the tiles grid-stride.  A tile writes its partial
+// sums to part[tile]; the block that completes the last tile of a graph
+// (per-graph arrival counter, reset by that block) adds the graph's partials
+// in tile order and takes the graph's decision in the same launch.  The
+// result does not depend on which block finishes last.
+struct LsTiles {
+  const int4* tiles;          // graph x, first row y, rows z
+  const int32_t* graph_tile;  // [G+1] first tile of each graph
+  int n;
+  unsigned* arrive;           // [G] tiles of the graph done in this launch
+  double* part;               // [n][PS] per-tile partial sums
+  int PS;
+};
+
+__device__ __forceinline__ bool ls_arrive(unsigned* arrive, int b, int ntiles) {
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&arrive[b], 1u) == (unsigned)(ntiles - 1);
+  __syncthreads();
+  const bool last = s_last != 0;
+  if (last) __threadfence();
+  return last;
 }
 
-// One value per tile summed per graph: lanes take every 32nd tile, then a
-// fixed shuffle tree; every lane returns the total.
-__device__ __forceinline__ double ls_warp_total(const double* __restrict__ part, int PS, int t0, int t1) {
-  const int lane = threadIdx.x & 31;
+// nv (<= 256) sums of the graph's tile partials [t0, t1) into out: thread j
+// adds entry j mod nv of every (256 / nv)-th tile starting at t0 + j / nv,
+// then the groups are added in order
+__device__ __forceinline__ void ls_graph_sums(const double* part, int PS, int t0, int t1, int nv, double* out) {
+  __shared__ double s_g[kLsTile];
+  const int groups = kLsTile / nv;
+  const int v = threadIdx.x % nv, grp = threadIdx.x / nv;
   double s = 0.0;
-  for (int t = t0 + lane; t < t1; t += 32) s += part[(size_t)t * PS];
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  return s;
-}
-
-// ------------------------------------------------------- row kernels ---
-// The gradient rows of a tile, egrad = (p/D) Delta - (p lambda/D) phi_p(u)
-// with its graph's coefficients (from the kept Delta rows Dl), and the tile's
-// share of U^T egrad.
-__global__ void __launch_bounds__(kLsTile) ls_grad_gram_kernel(const float* __restrict__ U,
-                                                               const float* __restrict__ Dl, float* egrad,
-                                                               int k, const double* __restrict__ gs, float pm2,
-                                                               const int4* __restrict__ tiles, const int* skip,
-                                                               double* part, int PS) {
-  const int4 td = ls_tile(tiles);
-  if (skip[td.x]) return;
-  __shared__ float sa[kLsTile * kMaxK], sb[kLsTile * kMaxK];
-  __shared__ float cA[kMaxK], cB[kMaxK];
-  if ((int)threadIdx.x < k) {
-    const double* g = gs + (size_t)td.x * kGsStride;
-    cA[threadIdx.x] = (float)g[kGsC0 + threadIdx.x];
-    cB[threadIdx.x] = (float)g[kGsC1 + threadIdx.x];
+  if (grp < groups)
+    for (int t = t0 + grp; t < t1; t += groups) s += __ldcg(&part[(size_t)t * PS + v]);
+  s_g[threadIdx.x] = s;
+  __syncthreads();
+  if ((int)threadIdx.x < nv) {
+    double tot = 0.0;
+    for (int q = 0; q < groups; ++q) tot += s_g[q * nv + threadIdx.x];
+    out[threadIdx.x] = tot;
   }
   __syncthreads();
-  const int64_t e0 = (int64_t)td.y * k;
-  const int cnt = td.z * k;
-  for (int e = threadIdx.x; e < cnt; e += kLsTile) {
-    const int c = e % k;
-    const float u = U[e0 + e];
-    const float phu = abs_pow_pm2_clamped(u, pm2) * u;
-    const float gv = cA[c] * Dl[e0 + e] - cB[c] * phu;
-    egrad[e0 + e] = gv;
-    sa[e] = u;
-    sb[e] = gv;
-  }
+}
+
+// one sum of the graph's tile partials: thread j takes tiles t0 + j,
+// t0 + j + 256, ..., then a fixed tree; every thread returns the total
+__device__ __forceinline__ double ls_graph_sum1(const double* part, int PS, int t0, int t1) {
+  __shared__ double s_r[kLsTile];
+  double s = 0.0;
+  for (int t = t0 + threadIdx.x; t < t1; t += kLsTile) s += __ldcg(&part[(size_t)t * PS]);
+  s_r[threadIdx.x] = s;
   __syncthreads();
-  ls_tile_gram(sa, sb, td.z, k, part + (size_t)blockIdx.x * PS);
-}
-
-// The Hessian-product rows of a tile from the edge kernel's sparse part S
-// (held in HV, overwritten), HV = A (S - lambda |u|^(p-2) v) - B (Delta sigma_D
-// + phi_p(u) E) with its graph's coefficients, and the tile's share of U^T HV.
-__global__ void __launch_bounds__(kLsTile) ls_hvp_gram_kernel(const float* __restrict__ U,
-                                                              const float* __restrict__ V,
-                                                              const float* __restrict__ Dl, float* HV, int k,
-                                                              const double* __restrict__ gs, float pm2,
-                                                              const int4* __restrict__ tiles, const int* skip,
-                                                              double* part, int PS) {
-  const int4 td = ls_tile(tiles);
-  if (skip[td.x]) return;
-  __shared__ float sa[kLsTile * kMaxK], sb[kLsTile * kMaxK];
-  __shared__ HvpCoef cf[kMaxK];
-  if ((int)threadIdx.x < k) {
-    const double* g = gs + (size_t)td.x * kGsStride;
-    const int c = threadIdx.x;
-    cf[c] = HvpCoef{(float)g[kGsC0 + c], (float)g[kGsC1 + c], (float)g[kGsC2 + c], (float)g[kGsC3 + c],
-                    (float)g[kGsC4 + c]};
+  for (int w = kLsTile / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) s_r[threadIdx.x] += s_r[threadIdx.x + w];
+    __syncthreads();
   }
+  const double total = s_r[0];
   __syncthreads();
-  const bool zero_rule = pm2 != 0.0f;
-  const int64_t e0 = (int64_t)td.y * k;
-  const int cnt = td.z * k;
-  for (int e = threadIdx.x; e < cnt; e += kLsTile) {
-    const int c = e % k;
-    const float u = U[e0 + e];
-    const float h = hvp_entry(HV[e0 + e], u, V[e0 + e], Dl[e0 + e], cf[c], pm2, zero_rule);
-    HV[e0 + e] = h;
-    sa[e] = u;
-    sb[e] = h;
-  }
-  __syncthreads();
-  ls_tile_gram(sa, sb, td.z, k, part + (size_t)blockIdx.x * PS);
+  return total;
 }
 
-// The tile's share of A^T B.
-__global__ void __launch_bounds__(kLsTile) ls_gram_kernel(const float* __restrict__ A,
-                                                          const float* __restrict__ B, int k,
-                                                          const int4* __restrict__ tiles, const int* skip,
-                                                          double* part, int PS) {
-  const int4 td = ls_tile(tiles);
-  if (skip[td.x]) return;
-  __shared__ float sa[kLsTile * kMaxK], sb[kLsTile * kMaxK];
-  ls_stage(sa, A, td.y, td.z, k);
-  ls_stage(sb, B, td.y, td.z, k);
-  __syncthreads();
-  ls_tile_gram(sa, sb, td.z, k, part + (size_t)blockIdx.x * PS);
-}
-
-// rg = egrad - U M (M = U^T egrad of the graph) and the tile's <rg, rg>.
-__global__ void __launch_bounds__(kLsTile) ls_proj_dot_kernel(float* rg, const float* __restrict__ egrad,
-                                                              const float* __restrict__ U, const double* sc,
-                                                              int stride, int M_off, int k,
-                                                              const int4* __restrict__ tiles, const int* skip,
-                                                              double* part, int PS) {
-  const int4 td = ls_tile(tiles);
-  if (skip[td.x]) return;
-  __shared__ float su[kLsTile * kMaxK];
-  __shared__ float sm[kMaxK * kMaxK];
-  __shared__ double s_out[1];
-  ls_stage(su, U, td.y, td.z, k);
-  ls_stage_matrix(sm, sc + (size_t)td.x * stride + M_off, k);
-  __syncthreads();
-  const int64_t e0 = (int64_t)td.y * k;
-  const int cnt = td.z * k;
-  Kahan acc;
-  acc.init();
-  for (int e = threadIdx.x; e < cnt; e += kLsTile) {
-    const int r = e / k, c = e - (e / k) * k;
-    float v = egrad[e0 + e];
-    for (int a = 0; a < k; ++a) v -= su[r * k + a] * sm[a * k + c];
-    rg[e0 + e] = v;
-    acc.add(v * v);
-  }
-  float2 v1[1] = {kahan_to_ff(acc)};
-  ls_block_sum<1>(v1, s_out);
-  if (threadIdx.x == 0) part[(size_t)blockIdx.x * PS] = s_out[0];
-}
-
-// The Riemannian Hessian's rows Hd = He - U Gm - delta M (Gm = U^T He, M =
-// U^T egrad of the graph) and the tile's <delta, Hd>.
-__global__ void __launch_bounds__(kLsTile) ls_hess_kernel(float* Hd, const float* __restrict__ He,
-                                                          const float* __restrict__ U,
-                                                          const float* __restrict__ delta, const double* sc,
-                                                          int stride, int Gm_off, int M_off, int k,
-                                                          const int4* __restrict__ tiles, const int* skip,
-                                                          double* part, int PS) {
-  const int4 td = ls_tile(tiles);
-  if (skip[td.x]) return;
-  __shared__ float su[kLsTile * kMaxK], sd[kLsTile * kMaxK];
-  __shared__ float sg[kMaxK * kMaxK], sm[kMaxK * kMaxK];
-  __shared__ double s_out[1];
-  ls_stage(su, U, td.y, td.z, k);
-  ls_stage(sd, delta, td.y, td.z, k);
-  const double* s = sc + (size_t)td.x * stride;
-  ls_stage_matrix(sg, s + Gm_off, k);
-  ls_stage_matrix(sm, s + M_off, k);
-  __syncthreads();
-  const int64_t e0 = (int64_t)td.y * k;
-  const int cnt = td.z * k;
-  Kahan acc;
-  acc.init();
-  for (int e = threadIdx.x; e < cnt; e += kLsTile) {
-    const int r = e / k, c = e - (e / k) * k;
-    float v = He[e0 + e];
-    for (int a = 0; a < k; ++a) v -= su[r * k + a] * sg[a * k + c] + sd[r * k + a] * sm[a * k + c];
-    Hd[e0 + e] = v;
-    acc.add(sd[e] * v);
-  }
-  float2 v1[1] = {kahan_to_ff(acc)};
-  ls_block_sum<1>(v1, s_out);
-  if (threadIdx.x == 0) part[(size_t)blockIdx.x * PS] = s_out[0];
-}
-
-// eta += step delta, Heta += step Hd, and unless the step ended on the
-// boundary r += alpha Hd with the tile's <r, r>.
-__global__ void __launch_bounds__(kLsTile) ls_cg_update_kernel(float* eta, float* Heta, float* r,
-                                                               const float* __restrict__ delta,
-                                                               const float* __restrict__ Hd, int k,
-                                                               const int4* __restrict__ tiles, const int* skip,
-                                                               const LsState* st, double* part, int PS) {
-  const int4 td = ls_tile(tiles);
-  if (skip[td.x]) return;
-  __shared__ double s_out[1];
-  const float step = (float)st[td.x].step;
-  const float alpha = (float)st[td.x].alpha;
-  const bool bnd = st[td.x].boundary != 0;
-  const int64_t e0 = (int64_t)td.y * k;
-  const int cnt = td.z * k;
-  Kahan acc;
-  acc.init();
-  for (int e = threadIdx.x; e < cnt; e += kLsTile) {
-    const int64_t i = e0 + e;
-    const float h = Hd[i];
-    eta[i] += step * delta[i];
-    Heta[i] += step * h;
-    if (!bnd) {
-      const float rn = r[i] + alpha * h;
-      r[i] = rn;
-      acc.add(rn * rn);
-    }
-  }
-  float2 v1[1] = {kahan_to_ff(acc)};
-  ls_block_sum<1>(v1, s_out);
-  if (threadIdx.x == 0) part[(size_t)blockIdx.x * PS] = s_out[0];
-}
-
-// delta = -r + beta delta
-__global__ void __launch_bounds__(kLsTile) ls_direction_kernel(float* delta, const float* __restrict__ r, int k,
-                                                               const int4* __restrict__ tiles, const int* skip,
-                                                               const LsState* st) {
-  const int4 td = ls_tile(tiles);
-  if (skip[td.x]) return;
-  const float beta = (float)st[td.x].beta;
-  const int64_t e0 = (int64_t)td.y * k;
-  const int cnt = td.z * k;
-  for (int e = threadIdx.x; e < cnt; e += kLsTile) delta[e0 + e] = -r[e0 + e] + beta * delta[e0 + e];
-}
-
-// truncated CG's start: eta = 0, Heta = 0, r = rg, delta = -rg
-__global__ void __launch_bounds__(kLsTile) ls_tcg_init_kernel(float* eta, float* Heta, float* r, float* delta,
-                                                              const float* __restrict__ rg, int k,
-                                                              const int4* __restrict__ tiles, const int* skip) {
-  const int4 td = ls_tile(tiles);
-  if (skip[td.x]) return;
-  const int64_t e0 = (int64_t)td.y * k;
-  const int cnt = td.z * k;
-  for (int e = threadIdx.x; e < cnt; e += kLsTile) {
-    const float g = rg[e0 + e];
-    eta[e0 + e] = 0.f;
-    Heta[e0 + e] = 0.f;
-    r[e0 + e] = g;
-    delta[e0 + e] = -g;
-  }
-}
-
-// out = X + Y
-__global__ void __launch_bounds__(kLsTile) ls_add_kernel(float* out, const float* __restrict__ X,
-                                                         const float* __restrict__ Y, int k,
-                                                         const int4* __restrict__ tiles, const int* skip) {
-  const int4 td = ls_tile(tiles);
-  if (skip[td.x]) return;
-  const int64_t e0 = (int64_t)td.y * k;
-  const int cnt = td.z * k;
-  for (int e = threadIdx.x; e < cnt; e += kLsTile) out[e0 + e] = X[e0 + e] + Y[e0 + e];
-}
-
-// the tile's <rg, eta> and <eta, Heta> (the model's decrease)
-__global__ void __launch_bounds__(kLsTile) ls_dots2_kernel(const float* __restrict__ rg,
-                                                           const float* __restrict__ eta,
-                                                           const float* __restrict__ Heta, int k,
-                                                           const int4* __restrict__ tiles, const int* skip,
-                                                           double* part, int PS) {
-  const int4 td = ls_tile(tiles);
-  if (skip[td.x]) return;
-  __shared__ double s_out[2];
-  const int64_t e0 = (int64_t)td.y * k;
-  const int cnt = td.z * k;
-  Kahan a0, a1;
-  a0.init();
-  a1.init();
-  for (int e = threadIdx.x; e < cnt; e += kLsTile) {
-    const float x = eta[e0 + e];
-    a0.add(rg[e0 + e] * x);
-    a1.add(x * Heta[e0 + e]);
-  }
-  float2 v2[2] = {kahan_to_ff(a0), kahan_to_ff(a1)};
-  ls_block_sum<2>(v2, s_out);
-  if (threadIdx.x < 2) part[(size_t)blockIdx.x * PS + threadIdx.x] = s_out[threadIdx.x];
-}
-
-// out = A R^-1 (R^-1 upper triangular, the graph's); in place when out == A
-// (the tile is staged first)
-__global__ void __launch_bounds__(kLsTile) ls_rmul_kernel(float* out, const float* A, const double* sc,
-                                                          int stride, int R_off, int k,
-                                                          const int4* __restrict__ tiles, const int* skip) {
-  const int4 td = ls_tile(tiles);
-  if (skip[td.x]) return;
-  __shared__ float sa[kLsTile * kMaxK];
-  __shared__ float sr[kMaxK * kMaxK];
-  ls_stage(sa, A, td.y, td.z, k);
-  ls_stage_matrix(sr, sc + (size_t)td.x * stride + R_off, k);
-  __syncthreads();
-  const int64_t e0 = (int64_t)td.y * k;
-  const int cnt = td.z * k;
-  for (int e = threadIdx.x; e < cnt; e += kLsTile) {
-    const int r = e / k, c = e - (e / k) * k;
-    float v = 0.f;
-    for (int a = 0; a <= c; ++a) v += sa[r * k + a] * sr[a * k + c];
-    out[e0 + e] = v;
-  }
-}
-
-// the rows of every graph whose trial point was accepted move to the iterate
-__global__ void __launch_bounds__(kLsTile) ls_accept_rows_kernel(float* U, const float* __restrict__ Un,
-                                                                 float* eg, const float* __restrict__ egn,
-                                                                 float* dk, const float* __restrict__ dkn,
-                                                                 float* rg, const float* __restrict__ rgn, int k,
-                                                                 const int4* __restrict__ tiles,
-                                                                 const LsState* st) {
-  const int4 td = ls_tile(tiles);
-  if (!st[td.x].accept) return;
-  const int64_t e0 = (int64_t)td.y * k;
-  const int cnt = td.z * k;
-  for (int e = threadIdx.x; e < cnt; e += kLsTile) {
-    const int64_t i = e0 + e;
-    U[i] = Un[i];
-    eg[i] = egn[i];
-    dk[i] = dkn[i];
-    rg[i] = rgn[i];
-  }
-}
-
-// ------------------------------------------------- per-graph decisions ---
-// The curvature step of truncated CG from the graph's <delta, H delta>: alpha
-// = <r,r> / <delta,H delta>, or, on negative curvature or when the step would
-// leave the trust region, the step tau to the boundary.  A warp per graph.
-__global__ void __launch_bounds__(256) ls_hess_fin_kernel(const double* __restrict__ part, int PS,
-                                                          const int32_t* __restrict__ graph_tile, int G,
-                                                          const int* skip, LsState* st) {
-  const int b = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-  if (b >= G || skip[b]) return;
-  const double dHd = ls_warp_total(part, PS, graph_tile[b], graph_tile[b + 1]);
-  if ((threadIdx.x & 31) != 0) return;
-  LsState& s = st[b];
-  s.d_Hd = dHd;
-  const double D2 = s.cg_Delta * s.cg_Delta;
-  const double alpha = dHd != 0.0 ? s.rr / dHd : INFINITY;
-  const double e_Pe_new = s.e_Pe + 2.0 * alpha * s.e_Pd + alpha * alpha * s.d_Pd;
-  if (dHd <= 0.0 || e_Pe_new >= D2) {
-    s.step = (-s.e_Pd + sqrt(s.e_Pd * s.e_Pd + s.d_Pd * (D2 - s.e_Pe))) / s.d_Pd;
-    s.alpha = 0.0;
-    s.boundary = 1;
-    s.reason = dHd <= 0.0 ? 1 : 2;
-  } else {
-    s.step = alpha;
-    s.alpha = alpha;
-    s.e_Pe = e_Pe_new;
-  }
-}
-
-// The end of a CG iteration from the graph's new <r, r>: stop on the
-// boundary, at the residual threshold or at max_inner; otherwise beta and
-// the recurrences for <eta, delta> and <delta, delta>.  A stopped graph is
-// flagged in skip (left out of the rest of truncated CG).
-__global__ void __launch_bounds__(256) ls_cg_fin_kernel(const double* __restrict__ part, int PS,
-                                                        const int32_t* __restrict__ graph_tile, int G, int* skip,
-                                                        LsState* st, int max_inner) {
-  const int b = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-  if (b >= G || skip[b]) return;
-  const double rr_new = ls_warp_total(part, PS, graph_tile[b], graph_tile[b + 1]);
-  if ((threadIdx.x & 31) != 0) return;
-  LsState& s = st[b];
-  s.j += 1;
-  if (s.boundary) {
-    s.done = 1;
-  } else {
-    const double beta = rr_new / s.rr;
-    const double alpha_d = s.alpha;
-    s.rr = rr_new;
-    if (sqrt(rr_new) <= s.stop) {
-      s.done = 1;
-      s.reason = 3;
-    } else if (s.j >= max_inner) {
-      s.done = 1;
-      s.reason = 4;
-    } else {
-      s.beta = beta;
-      s.e_Pd = beta * (s.e_Pd + alpha_d * s.d_Pd);
-      s.d_Pd = rr_new + beta * beta * s.d_Pd;
-    }
-  }
-  if (s.done) skip[b] = 1;
-}
-
-// R^T R = Gram (Cholesky) and R^-1 of every graph, a thread per graph; a Gram
-// matrix that is not numerically positive definite marks the graph.
-__global__ void ls_chol_kernel(double* sc, int stride, int gram_off, int rinv_off, int k, const int* skip,
-                               LsState* st, int G) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= G || skip[b]) return;
-  const double* Gm = sc + (size_t)b * stride + gram_off;
-  double* Ri = sc + (size_t)b * stride + rinv_off;
+// R^T R = Gram (Cholesky) and R^-1, k x k, by one thread; a Gram matrix that
+// is not numerically positive definite sets *bad
+__device__ void ls_chol_inv(const double* Gm, int k, double* Ri, int* bad) {
   double R[kMaxK * kMaxK];
   for (int t = 0; t < k * k; ++t) R[t] = 0.0;
   for (int j = 0; j < k; ++j) {
     double d2 = Gm[j * k + j];
     for (int m = 0; m < j; ++m) d2 -= R[m * k + j] * R[m * k + j];
     if (!(d2 > 0.0)) {
-      st[b].chol_bad = 1;
+      *bad = 1;
       d2 = 1e-300;
     }
     const double d = sqrt(d2);
@@ -656,6 +346,414 @@ __global__ void ls_chol_kernel(double* sc, int stride, int gram_off, int rinv_of
   }
 }
 
+// ------------------------------------------------------- row kernels ---
+// The gradient rows of a tile, egrad = (p/D) Delta - (p lambda/D) phi_p(u)
+// with its graph's coefficients (from the kept Delta rows Dl), and the tile's
+// share of M = U^T egrad; the graph's last tile writes M.
+__global__ void __launch_bounds__(kLsTile) ls_grad_gram_kernel(const float* __restrict__ U,
+                                                               const float* __restrict__ Dl, float* egrad,
+                                                               int k, const double* __restrict__ gs, float pm2,
+                                                               LsTiles T, const int* skip, double* sc, int stride,
+                                                               int M_off) {
+  __shared__ float sa[kLsTile * kMaxK], sb[kLsTile * kMaxK];
+  __shared__ float cA[kMaxK], cB[kMaxK];
+  for (int tile = blockIdx.x; tile < T.n; tile += gridDim.x) {
+    const int4 td = __ldg(&T.tiles[tile]);
+    const int b = td.x;
+    if (skip[b]) continue;
+    __syncthreads();  // the previous tile's shared data has been used
+    if ((int)threadIdx.x < k) {
+      const double* g = gs + (size_t)b * kGsStride;
+      cA[threadIdx.x] = (float)g[kGsC0 + threadIdx.x];
+      cB[threadIdx.x] = (float)g[kGsC1 + threadIdx.x];
+    }
+    __syncthreads();
+    const int64_t e0 = (int64_t)td.y * k;
+    const int cnt = td.z * k;
+    for (int e = threadIdx.x; e < cnt; e += kLsTile) {
+      const int c = e % k;
+      const float u = U[e0 + e];
+      const float phu = abs_pow_pm2_clamped(u, pm2) * u;
+      const float gv = cA[c] * Dl[e0 + e] - cB[c] * phu;
+      egrad[e0 + e] = gv;
+      sa[e] = u;
+      sb[e] = gv;
+    }
+    __syncthreads();
+    ls_tile_gram(sa, sb, td.z, k, T.part + (size_t)tile * T.PS);
+    const int t0 = T.graph_tile[b], t1 = T.graph_tile[b + 1];
+    if (ls_arrive(T.arrive, b, t1 - t0)) {
+      ls_graph_sums(T.part, T.PS, t0, t1, k * k, sc + (size_t)b * stride + M_off);
+      if (threadIdx.x == 0) T.arrive[b] = 0u;
+    }
+  }
+}
+
+// The Hessian-product rows of a tile from the edge kernel's sparse part S
+// (held in HV, overwritten), HV = A (S - lambda |u|^(p-2) v) - B (Delta sigma_D
+// + phi_p(u) E) with its graph's coefficients, and the tile's share of
+// Gm = U^T HV; the graph's last tile writes Gm.
+__global__ void __launch_bounds__(kLsTile) ls_hvp_gram_kernel(const float* __restrict__ U,
+                                                              const float* __restrict__ V,
+                                                              const float* __restrict__ Dl, float* HV, int k,
+                                                              const double* __restrict__ gs, float pm2, LsTiles T,
+                                                              const int* skip, double* sc, int stride, int Gm_off) {
+  __shared__ float sa[kLsTile * kMaxK], sb[kLsTile * kMaxK];
+  __shared__ HvpCoef cf[kMaxK];
+  const bool zero_rule = pm2 != 0.0f;
+  for (int tile = blockIdx.x; tile < T.n; tile += gridDim.x) {
+    const int4 td = __ldg(&T.tiles[tile]);
+    const int b = td.x;
+    if (skip[b]) continue;
+    __syncthreads();
+    if ((int)threadIdx.x < k) {
+      const double* g = gs + (size_t)b * kGsStride;
+      const int c = threadIdx.x;
+      cf[c] = HvpCoef{(float)g[kGsC0 + c], (float)g[kGsC1 + c], (float)g[kGsC2 + c], (float)g[kGsC3 + c],
+                      (float)g[kGsC4 + c]};
+    }
+    __syncthreads();
+    const int64_t e0 = (int64_t)td.y * k;
+    const int cnt = td.z * k;
+    for (int e = threadIdx.x; e < cnt; e += kLsTile) {
+      const int c = e % k;
+      const float u = U[e0 + e];
+      const float h = hvp_entry(HV[e0 + e], u, V[e0 + e], Dl[e0 + e], cf[c], pm2, zero_rule);
+      HV[e0 + e] = h;
+      sa[e] = u;
+      sb[e] = h;
+    }
+    __syncthreads();
+    ls_tile_gram(sa, sb, td.z, k, T.part + (size_t)tile * T.PS);
+    const int t0 = T.graph_tile[b], t1 = T.graph_tile[b + 1];
+    if (ls_arrive(T.arrive, b, t1 - t0)) {
+      ls_graph_sums(T.part, T.PS, t0, t1, k * k, sc + (size_t)b * stride + Gm_off);
+      if (threadIdx.x == 0) T.arrive[b] = 0u;
+    }
+  }
+}
+
+// The tile's share of A^T A; the graph's last tile writes the Gram matrix and
+// its Cholesky factor's inverse R^-1 (Cholesky-QR).
+__global__ void __launch_bounds__(kLsTile) ls_gram_chol_kernel(const float* __restrict__ A, int k, LsTiles T,
+                                                               const int* skip, double* sc, int stride,
+                                                               int gram_off, int rinv_off, LsState* st) {
+  __shared__ float sa[kLsTile * kMaxK];
+  for (int tile = blockIdx.x; tile < T.n; tile += gridDim.x) {
+    const int4 td = __ldg(&T.tiles[tile]);
+    const int b = td.x;
+    if (skip[b]) continue;
+    __syncthreads();
+    ls_stage(sa, A, td.y, td.z, k);
+    __syncthreads();
+    ls_tile_gram(sa, sa, td.z, k, T.part + (size_t)tile * T.PS);
+    const int t0 = T.graph_tile[b], t1 = T.graph_tile[b + 1];
+    if (ls_arrive(T.arrive, b, t1 - t0)) {
+      double* x = sc + (size_t)b * stride;
+      ls_graph_sums(T.part, T.PS, t0, t1, k * k, x + gram_off);
+      if (threadIdx.x == 0) {
+        ls_chol_inv(x + gram_off, k, x + rinv_off, &st[b].chol_bad);
+        T.arrive[b] = 0u;
+      }
+    }
+  }
+}
+
+// rg = egrad - U M (M = U^T egrad of the graph) and the tile's <rg, rg>; the
+// graph's last tile writes <rg, rg>.
+__global__ void __launch_bounds__(kLsTile) ls_proj_dot_kernel(float* rg, const float* __restrict__ egrad,
+                                                              const float* __restrict__ U, double* sc, int stride,
+                                                              int M_off, int gd_off, int k, LsTiles T,
+                                                              const int* skip) {
+  __shared__ float su[kLsTile * kMaxK];
+  __shared__ float sm[kMaxK * kMaxK];
+  __shared__ double s_out[1];
+  for (int tile = blockIdx.x; tile < T.n; tile += gridDim.x) {
+    const int4 td = __ldg(&T.tiles[tile]);
+    const int b = td.x;
+    if (skip[b]) continue;
+    __syncthreads();
+    ls_stage(su, U, td.y, td.z, k);
+    ls_stage_matrix(sm, sc + (size_t)b * stride + M_off, k);
+    __syncthreads();
+    const int64_t e0 = (int64_t)td.y * k;
+    const int cnt = td.z * k;
+    Kahan acc;
+    acc.init();
+    for (int e = threadIdx.x; e < cnt; e += kLsTile) {
+      const int r = e / k, c = e - (e / k) * k;
+      float v = egrad[e0 + e];
+      for (int a = 0; a < k; ++a) v -= su[r * k + a] * sm[a * k + c];
+      rg[e0 + e] = v;
+      acc.add(v * v);
+    }
+    float2 v1[1] = {kahan_to_ff(acc)};
+    ls_block_sum<1>(v1, s_out);
+    if (threadIdx.x == 0) T.part[(size_t)tile * T.PS] = s_out[0];
+    const int t0 = T.graph_tile[b], t1 = T.graph_tile[b + 1];
+    if (ls_arrive(T.arrive, b, t1 - t0)) {
+      const double tot = ls_graph_sum1(T.part, T.PS, t0, t1);
+      if (threadIdx.x == 0) {
+        sc[(size_t)b * stride + gd_off] = tot;
+        T.arrive[b] = 0u;
+      }
+    }
+  }
+}
+
+// The Riemannian Hessian's rows Hd = He - U Gm - delta M (Gm = U^T He, M =
+// U^T egrad of the graph) and the tile's <delta, Hd>.  The graph's last tile
+// takes truncated CG's curvature step: alpha = <r,r> / <delta, H delta>, or,
+// on negative curvature or when the step would leave the trust region, the
+// step tau to the boundary.
+__global__ void __launch_bounds__(kLsTile) ls_hess_kernel(float* Hd, const float* __restrict__ He,
+                                                          const float* __restrict__ U,
+                                                          const float* __restrict__ delta, const double* sc,
+                                                          int stride, int Gm_off, int M_off, int k, LsTiles T,
+                                                          const int* skip, LsState* st) {
+  __shared__ float su[kLsTile * kMaxK], sd[kLsTile * kMaxK];
+  __shared__ float sg[kMaxK * kMaxK], sm[kMaxK * kMaxK];
+  __shared__ double s_out[1];
+  for (int tile = blockIdx.x; tile < T.n; tile += gridDim.x) {
+    const int4 td = __ldg(&T.tiles[tile]);
+    const int b = td.x;
+    if (skip[b]) continue;
+    __syncthreads();
+    ls_stage(su, U, td.y, td.z, k);
+    ls_stage(sd, delta, td.y, td.z, k);
+    const double* x = sc + (size_t)b * stride;
+    ls_stage_matrix(sg, x + Gm_off, k);
+    ls_stage_matrix(sm, x + M_off, k);
+    __syncthreads();
+    const int64_t e0 = (int64_t)td.y * k;
+    const int cnt = td.z * k;
+    Kahan acc;
+    acc.init();
+    for (int e = threadIdx.x; e < cnt; e += kLsTile) {
+      const int r = e / k, c = e - (e / k) * k;
+      float v = He[e0 + e];
+      for (int a = 0; a < k; ++a) v -= su[r * k + a] * sg[a * k + c] + sd[r * k + a] * sm[a * k + c];
+      Hd[e0 + e] = v;
+      acc.add(sd[e] * v);
+    }
+    float2 v1[1] = {kahan_to_ff(acc)};
+    ls_block_sum<1>(v1, s_out);
+    if (threadIdx.x == 0) T.part[(size_t)tile * T.PS] = s_out[0];
+    const int t0 = T.graph_tile[b], t1 = T.graph_tile[b + 1];
+    if (ls_arrive(T.arrive, b, t1 - t0)) {
+      const double dHd = ls_graph_sum1(T.part, T.PS, t0, t1);
+      if (threadIdx.x == 0) {
+        LsState& q = st[b];
+        q.d_Hd = dHd;
+        const double D2 = q.cg_Delta * q.cg_Delta;
+        const double alpha = dHd != 0.0 ? q.rr / dHd : INFINITY;
+        const double e_Pe_new = q.e_Pe + 2.0 * alpha * q.e_Pd + alpha * alpha * q.d_Pd;
+        if (dHd <= 0.0 || e_Pe_new >= D2) {
+          q.step = (-q.e_Pd + sqrt(q.e_Pd * q.e_Pd + q.d_Pd * (D2 - q.e_Pe))) / q.d_Pd;
+          q.alpha = 0.0;
+          q.boundary = 1;
+          q.reason = dHd <= 0.0 ? 1 : 2;
+        } else {
+          q.step = alpha;
+          q.alpha = alpha;
+          q.e_Pe = e_Pe_new;
+        }
+        T.arrive[b] = 0u;
+      }
+    }
+  }
+}
+
+// eta += step delta, Heta += step Hd, and unless the step ended on the
+// boundary r += alpha Hd with the tile's <r, r>.  The graph's last tile ends
+// the CG iteration: stop on the boundary, at the residual threshold or at
+// max_inner (the graph is then flagged in skip); otherwise beta and the
+// recurrences for <eta, delta> and <delta, delta>.
+__global__ void __launch_bounds__(kLsTile) ls_cg_update_kernel(float* eta, float* Heta, float* r,
+                                                               const float* __restrict__ delta,
+                                                               const float* __restrict__ Hd, int k, LsTiles T,
+                                                               int* skip, LsState* st, int max_inner) {
+  __shared__ double s_out[1];
+  for (int tile = blockIdx.x; tile < T.n; tile += gridDim.x) {
+    const int4 td = __ldg(&T.tiles[tile]);
+    const int b = td.x;
+    if (skip[b]) continue;
+    const float step = (float)st[b].step;
+    const float alpha = (float)st[b].alpha;
+    const bool bnd = st[b].boundary != 0;
+    const int64_t e0 = (int64_t)td.y * k;
+    const int cnt = td.z * k;
+    Kahan acc;
+    acc.init();
+    for (int e = threadIdx.x; e < cnt; e += kLsTile) {
+      const int64_t i = e0 + e;
+      const float h = Hd[i];
+      eta[i] += step * delta[i];
+      Heta[i] += step * h;
+      if (!bnd) {
+        const float rn = r[i] + alpha * h;
+        r[i] = rn;
+        acc.add(rn * rn);
+      }
+    }
+    float2 v1[1] = {kahan_to_ff(acc)};
+    ls_block_sum<1>(v1, s_out);
+    if (threadIdx.x == 0) T.part[(size_t)tile * T.PS] = s_out[0];
+    const int t0 = T.graph_tile[b], t1 = T.graph_tile[b + 1];
+    if (ls_arrive(T.arrive, b, t1 - t0)) {
+      const double rr_new = ls_graph_sum1(T.part, T.PS, t0, t1);
+      if (threadIdx.x == 0) {
+        LsState& q = st[b];
+        q.j += 1;
+        if (q.boundary) {
+          q.done = 1;
+        } else {
+          const double beta = rr_new / q.rr;
+          const double alpha_d = q.alpha;
+          q.rr = rr_new;
+          if (sqrt(rr_new) <= q.stop) {
+            q.done = 1;
+            q.reason = 3;
+          } else if (q.j >= max_inner) {
+            q.done = 1;
+            q.reason = 4;
+          } else {
+            q.beta = beta;
+            q.e_Pd = beta * (q.e_Pd + alpha_d * q.d_Pd);
+            q.d_Pd = rr_new + beta * beta * q.d_Pd;
+          }
+        }
+        if (q.done) skip[b] = 1;
+        T.arrive[b] = 0u;
+      }
+    }
+  }
+}
+
+// delta = -r + beta delta
+__global__ void __launch_bounds__(kLsTile) ls_direction_kernel(float* delta, const float* __restrict__ r, int k,
+                                                               LsTiles T, const int* skip, const LsState* st) {
+  for (int tile = blockIdx.x; tile < T.n; tile += gridDim.x) {
+    const int4 td = __ldg(&T.tiles[tile]);
+    if (skip[td.x]) continue;
+    const float beta = (float)st[td.x].beta;
+    const int64_t e0 = (int64_t)td.y * k;
+    const int cnt = td.z * k;
+    for (int e = threadIdx.x; e < cnt; e += kLsTile) delta[e0 + e] = -r[e0 + e] + beta * delta[e0 + e];
+  }
+}
+
+// truncated CG's start: eta = 0, Heta = 0, r = rg, delta = -rg
+__global__ void __launch_bounds__(kLsTile) ls_tcg_init_kernel(float* eta, float* Heta, float* r, float* delta,
+                                                              const float* __restrict__ rg, int k, LsTiles T,
+                                                              const int* skip) {
+  for (int tile = blockIdx.x; tile < T.n; tile += gridDim.x) {
+    const int4 td = __ldg(&T.tiles[tile]);
+    if (skip[td.x]) continue;
+    const int64_t e0 = (int64_t)td.y * k;
+    const int cnt = td.z * k;
+    for (int e = threadIdx.x; e < cnt; e += kLsTile) {
+      const float g = rg[e0 + e];
+      eta[e0 + e] = 0.f;
+      Heta[e0 + e] = 0.f;
+      r[e0 + e] = g;
+      delta[e0 + e] = -g;
+    }
+  }
+}
+
+// out = X + Y
+__global__ void __launch_bounds__(kLsTile) ls_add_kernel(float* out, const float* __restrict__ X,
+                                                         const float* __restrict__ Y, int k, LsTiles T,
+                                                         const int* skip) {
+  for (int tile = blockIdx.x; tile < T.n; tile += gridDim.x) {
+    const int4 td = __ldg(&T.tiles[tile]);
+    if (skip[td.x]) continue;
+    const int64_t e0 = (int64_t)td.y * k;
+    const int cnt = td.z * k;
+    for (int e = threadIdx.x; e < cnt; e += kLsTile) out[e0 + e] = X[e0 + e] + Y[e0 + e];
+  }
+}
+
+// the tile's <rg, eta> and <eta, Heta> (the model's decrease); the graph's
+// last tile writes both
+__global__ void __launch_bounds__(kLsTile) ls_dots2_kernel(const float* __restrict__ rg,
+                                                           const float* __restrict__ eta,
+                                                           const float* __restrict__ Heta, int k, LsTiles T,
+                                                           const int* skip, double* sc, int stride, int dots_off) {
+  __shared__ double s_out[2];
+  for (int tile = blockIdx.x; tile < T.n; tile += gridDim.x) {
+    const int4 td = __ldg(&T.tiles[tile]);
+    const int b = td.x;
+    if (skip[b]) continue;
+    const int64_t e0 = (int64_t)td.y * k;
+    const int cnt = td.z * k;
+    Kahan a0, a1;
+    a0.init();
+    a1.init();
+    for (int e = threadIdx.x; e < cnt; e += kLsTile) {
+      const float x = eta[e0 + e];
+      a0.add(rg[e0 + e] * x);
+      a1.add(x * Heta[e0 + e]);
+    }
+    float2 v2[2] = {kahan_to_ff(a0), kahan_to_ff(a1)};
+    ls_block_sum<2>(v2, s_out);
+    if (threadIdx.x < 2) T.part[(size_t)tile * T.PS + threadIdx.x] = s_out[threadIdx.x];
+    const int t0 = T.graph_tile[b], t1 = T.graph_tile[b + 1];
+    if (ls_arrive(T.arrive, b, t1 - t0)) {
+      ls_graph_sums(T.part, T.PS, t0, t1, 2, sc + (size_t)b * stride + dots_off);
+      if (threadIdx.x == 0) T.arrive[b] = 0u;
+    }
+  }
+}
+
+// out = A R^-1 (R^-1 upper triangular, the graph's); in place when out == A
+// (the tile is staged first)
+__global__ void __launch_bounds__(kLsTile) ls_rmul_kernel(float* out, const float* A, const double* sc,
+                                                          int stride, int R_off, int k, LsTiles T,
+                                                          const int* skip) {
+  __shared__ float sa[kLsTile * kMaxK];
+  __shared__ float sr[kMaxK * kMaxK];
+  for (int tile = blockIdx.x; tile < T.n; tile += gridDim.x) {
+    const int4 td = __ldg(&T.tiles[tile]);
+    if (skip[td.x]) continue;
+    __syncthreads();
+    ls_stage(sa, A, td.y, td.z, k);
+    ls_stage_matrix(sr, sc + (size_t)td.x * stride + R_off, k);
+    __syncthreads();
+    const int64_t e0 = (int64_t)td.y * k;
+    const int cnt = td.z * k;
+    for (int e = threadIdx.x; e < cnt; e += kLsTile) {
+      const int r = e / k, c = e - (e / k) * k;
+      float v = 0.f;
+      for (int a = 0; a <= c; ++a) v += sa[r * k + a] * sr[a * k + c];
+      out[e0 + e] = v;
+    }
+  }
+}
+
+// the rows of every graph whose trial point was accepted move to the iterate
+__global__ void __launch_bounds__(kLsTile) ls_accept_rows_kernel(float* U, const float* __restrict__ Un,
+                                                                 float* eg, const float* __restrict__ egn,
+                                                                 float* dk, const float* __restrict__ dkn,
+                                                                 float* rg, const float* __restrict__ rgn, int k,
+                                                                 LsTiles T, const LsState* st) {
+  for (int tile = blockIdx.x; tile < T.n; tile += gridDim.x) {
+    const int4 td = __ldg(&T.tiles[tile]);
+    if (!st[td.x].accept) continue;
+    const int64_t e0 = (int64_t)td.y * k;
+    const int cnt = td.z * k;
+    for (int e = threadIdx.x; e < cnt; e += kLsTile) {
+      const int64_t i = e0 + e;
+      U[i] = Un[i];
+      eg[i] = egn[i];
+      dk[i] = dkn[i];
+      rg[i] = rgn[i];
+    }
+  }
+}
+
+// ------------------------------------------------- per-graph decisions ---
 // Opens the graph's next Newton step, or ends its stage: converged when
 // ||rg|| <= max(gtol_abs, gtol_rel ||rg_0||), ended at max_outer.  An open
 // step starts truncated CG at eta = 0 with the stopping threshold
@@ -869,7 +967,8 @@ struct LsWork {
   float* task_part = nullptr;
   double* row_cut = nullptr;
   double* rcut = nullptr;
-  int* h_flags = nullptr;  // pinned [2G]
+  unsigned* arrive = nullptr;  // [G] per-graph tile arrival counters (zero between launches)
+  int* h_flags = nullptr;      // pinned [2G]
   ~LsWork() {
     for (void* q : allocs) cudaFree(q);
     if (h_flags) cudaFreeHost(h_flags);
@@ -892,13 +991,9 @@ struct Lockstep {
   LsOpts o;
   int alg1 = 0;
   const int32_t* graph_task = nullptr;
-  int fin_blocks = 1;
+  LsTiles T;
+  int rows_blocks = 1;  // grid of the row kernels (they walk the tiles grid-stride)
 
-  pspec_status fin(int nv, const int* skip, int off) {
-    ls_fin_kernel<<<fin_blocks, 256, 0, s>>>(w.part, w.PS, w.graph_tile, G, nv, skip, w.sc, w.off.stride, off);
-    PSPEC_CUDA(cudaGetLastError());
-    return PSPEC_OK;
-  }
   // F, N, D, Delta_p u (kept in dk), the Euclidean gradient, M = U^T egrad
   // and the Riemannian gradient rg with <rg, rg>, for every graph not in
   // skip_newton
@@ -911,18 +1006,16 @@ struct Lockstep {
     TimedScope timer(g, "lockstep_eval_rows", s);
     ls_reduce_kernel<<<G, 256, 0, s>>>(w.task_part, graph_task, k, 0, p, 0, g->d_graph_scalars, w.sc,
                                        w.off.stride, nd_off, F_off, skip, w.st);
-    ls_grad_gram_kernel<<<w.n_tiles, kLsTile, 0, s>>>(U, dk, eg, k, g->d_graph_scalars, (float)p - 2.0f, w.tiles,
-                                                      skip, w.part, w.PS);
-    PSPEC_TRY(fin(kk, skip, M_off));
-    ls_proj_dot_kernel<<<w.n_tiles, kLsTile, 0, s>>>(rg, eg, U, w.sc, w.off.stride, M_off, k, w.tiles, skip,
-                                                     w.part, w.PS);
-    PSPEC_TRY(fin(1, skip, gd_off));
+    ls_grad_gram_kernel<<<rows_blocks, kLsTile, 0, s>>>(U, dk, eg, k, g->d_graph_scalars, (float)p - 2.0f, T,
+                                                        skip, w.sc, w.off.stride, M_off);
+    ls_proj_dot_kernel<<<rows_blocks, kLsTile, 0, s>>>(rg, eg, U, w.sc, w.off.stride, M_off, gd_off, k, T, skip);
+    PSPEC_CUDA(cudaGetLastError());
     return PSPEC_OK;
   }
   // one truncated-CG iteration of every graph not in skip_cg: the Hessian
-  // product at the iterate (its kept Delta_p u, N and D), U^T (H delta), the
-  // Riemannian Hessian, the curvature step, the updates of eta, H eta, r,
-  // the stopping tests and the new direction
+  // product at the iterate (its kept Delta_p u, N and D) with U^T (H delta),
+  // the Riemannian Hessian and the curvature step, the updates of eta, H eta
+  // and r with the stopping tests, and the new direction
   pspec_status cg_iter(double p) {
     const int* skip = w.skip_cg;
     EdgeLaunch L{w.U, w.delta, w.He, nullptr, p, k, nullptr, w.task_part};
@@ -930,19 +1023,30 @@ struct Lockstep {
     L.graph_skip = skip;
     L.alg1 = alg1 != 0;
     PSPEC_TRY(launch_hvp_edges(g, L, s));
-    TimedScope timer(g, "lockstep_tcg_rows", s);
-    ls_reduce_kernel<<<G, 256, 0, s>>>(w.task_part, graph_task, k, 1, p, alg1, g->d_graph_scalars, w.sc,
-                                       w.off.stride, w.off.nd, 0, skip, w.st);
-    ls_hvp_gram_kernel<<<w.n_tiles, kLsTile, 0, s>>>(w.U, w.delta, w.dk, w.He, k, g->d_graph_scalars,
-                                                     (float)p - 2.0f, w.tiles, skip, w.part, w.PS);
-    PSPEC_TRY(fin(kk, skip, w.off.Gm));
-    ls_hess_kernel<<<w.n_tiles, kLsTile, 0, s>>>(w.Hd, w.He, w.U, w.delta, w.sc, w.off.stride, w.off.Gm, w.off.M,
-                                                 k, w.tiles, skip, w.part, w.PS);
-    ls_hess_fin_kernel<<<fin_blocks, 256, 0, s>>>(w.part, w.PS, w.graph_tile, G, skip, w.st);
-    ls_cg_update_kernel<<<w.n_tiles, kLsTile, 0, s>>>(w.eta, w.Heta, w.r, w.delta, w.Hd, k, w.tiles, skip, w.st,
-                                                      w.part, w.PS);
-    ls_cg_fin_kernel<<<fin_blocks, 256, 0, s>>>(w.part, w.PS, w.graph_tile, G, w.skip_cg, w.st, o.max_inner);
-    ls_direction_kernel<<<w.n_tiles, kLsTile, 0, s>>>(w.delta, w.r, k, w.tiles, skip, w.st);
+    {
+      TimedScope timer(g, "ls_reduce", s);
+      ls_reduce_kernel<<<G, 256, 0, s>>>(w.task_part, graph_task, k, 1, p, alg1, g->d_graph_scalars, w.sc,
+                                         w.off.stride, w.off.nd, 0, skip, w.st);
+    }
+    {
+      TimedScope timer(g, "ls_hvp_gram", s);
+      ls_hvp_gram_kernel<<<rows_blocks, kLsTile, 0, s>>>(w.U, w.delta, w.dk, w.He, k, g->d_graph_scalars,
+                                                         (float)p - 2.0f, T, skip, w.sc, w.off.stride, w.off.Gm);
+    }
+    {
+      TimedScope timer(g, "ls_hess", s);
+      ls_hess_kernel<<<rows_blocks, kLsTile, 0, s>>>(w.Hd, w.He, w.U, w.delta, w.sc, w.off.stride, w.off.Gm,
+                                                     w.off.M, k, T, skip, w.st);
+    }
+    {
+      TimedScope timer(g, "ls_cg_update", s);
+      ls_cg_update_kernel<<<rows_blocks, kLsTile, 0, s>>>(w.eta, w.Heta, w.r, w.delta, w.Hd, k, T, w.skip_cg,
+                                                          w.st, o.max_inner);
+    }
+    {
+      TimedScope timer(g, "ls_direction", s);
+      ls_direction_kernel<<<rows_blocks, kLsTile, 0, s>>>(w.delta, w.r, k, T, skip, w.st);
+    }
     PSPEC_CUDA(cudaGetLastError());
     return PSPEC_OK;
   }
@@ -950,13 +1054,12 @@ struct Lockstep {
   pspec_status trial_point() {
     const int* skip = w.skip_newton;
     TimedScope timer(g, "lockstep_retraction", s);
-    ls_add_kernel<<<w.n_tiles, kLsTile, 0, s>>>(w.tmp, w.U, w.eta, k, w.tiles, skip);
+    ls_add_kernel<<<rows_blocks, kLsTile, 0, s>>>(w.tmp, w.U, w.eta, k, T, skip);
     const float* src = w.tmp;
     for (int pass = 0; pass < 2; ++pass) {
-      ls_gram_kernel<<<w.n_tiles, kLsTile, 0, s>>>(src, src, k, w.tiles, skip, w.part, w.PS);
-      PSPEC_TRY(fin(kk, skip, w.off.Gram));
-      ls_chol_kernel<<<(G + 127) / 128, 128, 0, s>>>(w.sc, w.off.stride, w.off.Gram, w.off.Rinv, k, skip, w.st, G);
-      ls_rmul_kernel<<<w.n_tiles, kLsTile, 0, s>>>(w.Un, src, w.sc, w.off.stride, w.off.Rinv, k, w.tiles, skip);
+      ls_gram_chol_kernel<<<rows_blocks, kLsTile, 0, s>>>(src, k, T, skip, w.sc, w.off.stride, w.off.Gram,
+                                                          w.off.Rinv, w.st);
+      ls_rmul_kernel<<<rows_blocks, kLsTile, 0, s>>>(w.Un, src, w.sc, w.off.stride, w.off.Rinv, k, T, skip);
       src = w.Un;
     }
     PSPEC_CUDA(cudaGetLastError());
@@ -1034,9 +1137,18 @@ pspec_status setup(Lockstep& S, const std::vector<int64_t>& off, int k) {
   PSPEC_TRY(w.alloc(&w.row_cut, g->n));
   PSPEC_TRY(w.alloc(&w.rcut, G));
   PSPEC_CUDA(cudaMallocHost(&w.h_flags, sizeof(int) * 2 * std::max(1, G)));
+  PSPEC_TRY(w.alloc(&w.arrive, G));
+  PSPEC_CUDA(cudaMemsetAsync(w.arrive, 0, sizeof(unsigned) * G, S.s));
+  S.T = LsTiles{w.tiles, w.graph_tile, w.n_tiles, w.arrive, w.part, w.PS};
+  // the row kernels' grid: one block per tile, or with
+  // PSPEC_LOCKSTEP_BLOCKS_PER_SM = b > 0 that many blocks per SM walking the
+  // tiles
+  int64_t rb = w.n_tiles;
+  if (const char* env = std::getenv("PSPEC_LOCKSTEP_BLOCKS_PER_SM"))
+    if (std::atoi(env) > 0) rb = std::min<int64_t>(rb, (int64_t)g->sm_count * std::atoi(env));
+  S.rows_blocks = (int)std::max<int64_t>(1, rb);
   ls_init_kernel<<<(G + 255) / 256, 256, 0, S.s>>>(w.st, w.valid, G);
   PSPEC_CUDA(cudaGetLastError());
-  S.fin_blocks = (G * 32 + 255) / 256;
   return PSPEC_OK;
 }
 
@@ -1058,8 +1170,8 @@ pspec_status run_stages(Lockstep& S, const double* sched, int n_p, int verbose) 
     int step = 0;
     while (active > 0) {
       ++step;
-      ls_tcg_init_kernel<<<w.n_tiles, kLsTile, 0, S.s>>>(w.eta, w.Heta, w.r, w.delta, w.rg, S.k, w.tiles,
-                                                          w.skip_cg);
+      ls_tcg_init_kernel<<<S.rows_blocks, kLsTile, 0, S.s>>>(w.eta, w.Heta, w.r, w.delta, w.rg, S.k, S.T,
+                                                              w.skip_cg);
       PSPEC_CUDA(cudaGetLastError());
       int chunks = 0;
       for (int it = 0; it < S.o.max_inner; it += chunk, ++chunks) {
@@ -1093,12 +1205,11 @@ pspec_status run_stages(Lockstep& S, const double* sched, int n_p, int verbose) 
       }
       PSPEC_TRY(S.trial_point());
       PSPEC_TRY(S.eval(w.Un, p, w.dkn, w.egn, w.rgn, w.off.ndn, w.off.Fn, w.off.Mn, w.off.gdn));
-      ls_dots2_kernel<<<w.n_tiles, kLsTile, 0, S.s>>>(w.rg, w.eta, w.Heta, S.k, w.tiles, w.skip_newton, w.part,
-                                                       w.PS);
-      PSPEC_TRY(S.fin(2, w.skip_newton, w.off.dots));
+      ls_dots2_kernel<<<S.rows_blocks, kLsTile, 0, S.s>>>(w.rg, w.eta, w.Heta, S.k, S.T, w.skip_newton, w.sc,
+                                                           w.off.stride, w.off.dots);
       ls_decide_kernel<<<1, 256, 0, S.s>>>(w.st, w.sc, w.off, S.o, S.kk, w.skip_newton, w.skip_cg, G);
-      ls_accept_rows_kernel<<<w.n_tiles, kLsTile, 0, S.s>>>(w.U, w.Un, w.eg, w.egn, w.dk, w.dkn, w.rg, w.rgn, S.k,
-                                                            w.tiles, w.st);
+      ls_accept_rows_kernel<<<S.rows_blocks, kLsTile, 0, S.s>>>(w.U, w.Un, w.eg, w.egn, w.dk, w.dkn, w.rg, w.rgn,
+                                                                S.k, S.T, w.st);
       PSPEC_CUDA(cudaGetLastError());
       const int before = active;
       PSPEC_TRY(S.count_open(w.skip_newton, &active));
