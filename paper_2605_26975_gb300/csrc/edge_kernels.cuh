@@ -81,8 +81,8 @@ struct EdgeArgs {
   // NULL: round-robin
   const int32_t* warp_begin;
   // batches: the tasks of graph q are left out while graph_skip[q] is
-  // nonzero (task_graph: the graph of each task); NULL: every task runs.
-  // The direct kernel only.
+  // nonzero (task_graph: the graph of each task); read only by the direct
+  // kernel's GSKIP instantiation
   const int* graph_skip;
   const int32_t* task_graph;
 };
@@ -355,8 +355,10 @@ __device__ __forceinline__ LaneTask lane_task(int4 task, int lane) {
 }
 
 // SPLIT: the warps take contiguous, cost-balanced task ranges (a.warp_begin)
-// instead of round-robin tasks
-template <int K, int MODE, bool SPLIT>
+// instead of round-robin tasks.  GSKIP: batch launches that leave out the
+// tasks of graphs flagged in a.graph_skip (a separate instantiation, so the
+// other launches carry no per-task test).
+template <int K, int MODE, bool SPLIT, bool GSKIP = false>
 __global__ void __launch_bounds__(kBlock, edge_min_blocks<K, MODE, SPLIT>()) edge_kernel(EdgeArgs a) {
   constexpr bool HVP = MODE != kModeEval;
   constexpr bool KEPT = MODE == kModeHvpKept;
@@ -389,7 +391,9 @@ __global__ void __launch_bounds__(kBlock, edge_min_blocks<K, MODE, SPLIT>()) edg
   const int t_first = SPLIT ? __ldg(&a.warp_begin[gwarp]) : gwarp;
   const int t_end = SPLIT ? __ldg(&a.warp_begin[gwarp + 1]) : a.n_tasks;
   for (int t = t_first; t < t_end; t += SPLIT ? 1 : nwarps) {
-    if (a.graph_skip && a.graph_skip[__ldg(&a.task_graph[t])]) continue;  // uniform over the warp
+    if constexpr (GSKIP) {
+      if (a.graph_skip[__ldg(&a.task_graph[t])]) continue;  // uniform over the warp
+    }
     const int4 task = __ldg(&a.tasks[t]);
     const LaneTask lt = lane_task<Q>(task, lane);
     const bool hub = lt.hub;

@@ -49,12 +49,13 @@ pspec_status launch_staged(pspec_graph* g, const EdgeArgs& a, int max_entries, i
 // assignments, so results stay bit-reproducible
 constexpr int kSplitTasksPerWarp = 8;
 
-template <int K, int MODE, bool SPLIT>
+template <int K, int MODE, bool SPLIT, bool GSKIP = false>
 int direct_blocks(pspec_graph* g, int64_t n_tasks, int want) {
   // resident blocks at the kernel's register count, once per process
   static const int occ_direct = [] {
     int o = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, edge_kernel<K, MODE, SPLIT>, kBlock, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, edge_kernel<K, MODE, SPLIT, GSKIP>, kBlock, 0) !=
+        cudaSuccess)
       o = 1;
     return std::max(o, 1);
   }();
@@ -66,8 +67,16 @@ int direct_blocks(pspec_graph* g, int64_t n_tasks, int want) {
 template <int K, int MODE>
 pspec_status launch_direct(pspec_graph* g, EdgeArgs a, TaskSet& ts, int want, cudaStream_t s) {
   const int64_t n_tasks = ts.n_tasks;
-  const int rr_blocks = direct_blocks<K, MODE, false>(g, n_tasks, want);
   a.warp_begin = nullptr;
+  if (a.graph_skip) {
+    // round-robin tasks: a graph's (contiguous) tasks spread over all warps,
+    // so a launch in which few graphs take part is not left to a few warps
+    const int blocks = direct_blocks<K, MODE, false, true>(g, n_tasks, want);
+    edge_kernel<K, MODE, false, true><<<blocks, kBlock, 0, s>>>(a);
+    PSPEC_CUDA(cudaGetLastError());
+    return PSPEC_OK;
+  }
+  const int rr_blocks = direct_blocks<K, MODE, false>(g, n_tasks, want);
   if (n_tasks < (int64_t)kSplitTasksPerWarp * rr_blocks * kWarps) {
     const int blocks = direct_blocks<K, MODE, true>(g, n_tasks, want);
     PSPEC_TRY(ensure_split(ts, blocks * kWarps, s, &a.warp_begin));
