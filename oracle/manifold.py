@@ -2,10 +2,10 @@
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
-The paper (Section 2) minimises Eq. 1 "for progressively smaller values of p
-using Newton's method on the Grassmann manifold", the Newton subproblems
-solved by truncated conjugate gradients (ROPTLIB, fed with EucGrad and
-EucHessianEta).  It prints no further detail, so the following readings are
+The paper (Section 2) minimises Eq. 1 on the Grassmann manifold with Newton's
+method, one solve per p with p lowered stage by stage toward 1, and solves the
+Newton subproblems by truncated conjugate gradients (in ROPTLIB, given the
+Euclidean gradient and Hessian-vector product).  It prints no further detail, so the following readings are
 taken, each the textbook form (Absil, Mahony & Sepulchre, "Optimization
 Algorithms on Matrix Manifolds", 2008: the Riemannian trust-region method and
 its Steihaug-Toint truncated CG; Edelman, Arias & Smith 1998 for the

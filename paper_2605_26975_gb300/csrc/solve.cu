@@ -1,6 +1,6 @@
 // pspec_solve: the paper's solve (Section 2) -- F_p minimised on the
-// Grassmann manifold by Newton's method with truncated-CG subproblems, "for
-// progressively smaller values of p" -- followed by k-means and RCut.
+// Grassmann manifold by Newton's method with truncated-CG subproblems, with p
+// lowered stage by stage from 2 toward 1 -- followed by k-means and RCut.
 //
 // Reading taken (the paper delegates these to ROPTLIB and prints no detail;
 // the CPU oracle follows the same reading): the Riemannian trust-region

@@ -1,5 +1,5 @@
 // pspec_solve_batched: the solve of Section 2 (Newton/tCG on the Grassmann
-// manifold for progressively smaller p, then k-means and RCut) for every
+// manifold, p lowered stage by stage toward 1, then k-means and RCut) for every
 // graph of a batched handle, each graph its own problem.
 //
 // Each graph gets a single-graph handle of its own (built on the first call

@@ -1,7 +1,7 @@
 // pspec_solve_lockstep: the solve of Section 2 -- trust-region Newton with
-// truncated-CG subproblems on the Grassmann manifold for progressively
-// smaller p, then k-means and RCut -- for every graph of a batched handle at
-// once, in lockstep.
+// truncated-CG subproblems on the Grassmann manifold, p lowered stage by
+// stage toward 1, then k-means and RCut -- for every graph of a batched handle
+// at once, in lockstep.
 //
 // One launch serves the whole batch at every step: each evaluation and each
 // Hessian product is one launch of the edge kernel over the concatenated CSR
