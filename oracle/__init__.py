@@ -12,12 +12,12 @@ with numpy.  Where the paper is silent the module docstrings state the reading
 taken.  The pins that tie each function to something other than itself live in
 ``tests/test_oracle_*.py``.
 
-Parity status: every function is pinned except the p < 2 stages of the solve,
-which the method reaches by a heuristic continuation with no closed form
-("parity unpinned" for ``manifold.solve`` below p = 2, with either Hessian
-form; it is checked only by agreement of the two implementations and by its
-p = 2 stage, where the exact and Algorithm 1 forms give the same projected
-Hessian).
+Parity status: every function is pinned.  The p < 2 stages of the solve, a
+continuation with no closed form, are pinned on special cases: the local
+quadratic convergence of Newton with the exact Hessian near a smooth
+minimiser, and the known global minimum (F_p = 0, RCut = 0) on graphs with k
+connected components.  The path through a whole schedule is checked by
+agreement of the two implementations.
 """
 from .plap import (edge_list, phi_p, abs_pow_pm2, p_norm_p, objective_parts, objective,
                    p_laplacian, euclidean_grad, euclidean_hvp, alg1_sparse_hvp)

@@ -127,7 +127,8 @@ def tcg(hess, grad, Delta, theta, kappa, max_inner):
 def rtr_newton(g, U, p, opts: SolveOptions):
     """Trust-region Newton on Gr(k, n) for F_p at fixed p, from U.
 
-    Returns (U, stats) with stats a dict: outer, inner, f, gnorm, gnorm0.
+    Returns (U, stats) with stats a dict: outer, inner, f, gnorm, gnorm0 and
+    history, the ||rg|| of the iterate after each Newton step.
     """
     k = U.shape[1]
     Delta_bar = opts.delta_bar_scale * math.sqrt(k)
@@ -142,6 +143,7 @@ def rtr_newton(g, U, p, opts: SolveOptions):
     gnorm0 = gnorm
     outer = 0
     inner_total = 0
+    history = []
     while outer < opts.max_outer:
         if gnorm <= max(opts.gtol_abs, opts.gtol_rel * gnorm0):
             break
@@ -171,8 +173,9 @@ def rtr_newton(g, U, p, opts: SolveOptions):
             f, egrad = value_grad(U)
             rg = project(U, egrad)
             gnorm = math.sqrt(inner(rg, rg))
+        history.append(gnorm)
     return U, dict(outer=outer, inner=inner_total, f=f, gnorm=gnorm, gnorm0=gnorm0,
-                   delta=Delta)
+                   delta=Delta, history=history)
 
 
 def solve(g, U0, p_schedule, opts: SolveOptions | None = None, n_clusters=None):

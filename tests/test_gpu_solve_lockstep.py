@@ -200,3 +200,32 @@ def test_lockstep_zero_column_stops_only_its_graph(api):
     _, _, rc0, st0, _ = S.solve(torch.from_numpy(U[:gs[0].n]).cuda(), [2.0, 1.5])
     assert abs(stats[0]["f"][0] - st0["f"][0]) <= 1e-5 * st0["f"][0]
     assert abs(rc[0] - rc0) <= 0.01 * rc0
+
+
+def test_solves_below_p2_reach_the_component_optimum(api):
+    """Graphs with exactly k connected components, where F_p = 0 on the span of
+    the component indicators for every p: from a perturbed indicator block, the
+    p < 2 stages of pspec_solve and of the lockstep solve end on the components
+    with RCut = 0, as the oracle does."""
+    from test_oracle_manifold import components_graph
+    k = 3
+    gs, comps, U0s = [], [], []
+    for seed, sizes in ((3, [30, 24, 36]), (4, [300, 240, 410]), (5, [1200, 900, 1500])):
+        g, comp = components_graph(sizes, seed)
+        g = wl.CSRGraph(g.n, g.rowptr, g.col, g.val.astype(np.float32))
+        ind = np.zeros((g.n, k))
+        ind[np.arange(g.n), comp] = 1.0
+        U0 = oracle.qf(ind + 0.2 * np.random.default_rng(seed).standard_normal(ind.shape)).astype(np.float32)
+        gs.append(g), comps.append(comp), U0s.append(U0)
+    sched = (1.6, 1.3)
+    for g, comp, U0 in zip(gs, comps, U0s):
+        S = api.Graph.from_csr(g)
+        _, lab, rc, st, _ = S.solve(torch.from_numpy(U0).cuda(), sched, api.default_opts(max_outer=60))
+        assert rc == 0.0 and same_partition(lab.cpu().numpy(), comp)
+    batch = wl.concat_graphs(gs, [k] * len(gs))
+    G = handle(api, batch)
+    _, lab, rc, status, stats, _ = G.solve_lockstep(torch.from_numpy(np.concatenate(U0s)).cuda(), sched,
+                                                    api.default_opts(max_outer=60))
+    for i, comp in enumerate(comps):
+        a, b = batch.node_off[i], batch.node_off[i + 1]
+        assert rc[i] == 0.0 and same_partition(lab[a:b].cpu().numpy(), comp), i

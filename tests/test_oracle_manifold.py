@@ -242,3 +242,97 @@ def test_alg1_hessian_form_is_exact_on_tangent_vectors_at_p2():
     U1, st = oracle.rtr_newton(g, wl.orthonormal_block(9, n, k, np.float64), 2.0, opts)
     ev = np.linalg.eigvalsh(laplacian(Wd))
     assert math.isclose(oracle.objective(g, U1, 2.0), ev[:k].sum(), rel_tol=1e-8)
+
+
+# ---- p < 2 stages pinned on graphs with k connected components: F_p >= 0,
+# and F_p = 0 exactly when every column is constant on every component, so
+# the span of the component indicators is the global minimum for every p.
+# (F_p is not smooth at ties for p < 2, so the approach is slow: the pins are
+# bounds, with margins over what the reading reaches.)
+def components_graph(sizes, seed):
+    """Cycles with random chords, one per size, weights U[0.5, 1.5]: exactly
+    len(sizes) connected components.  Returns the graph and each vertex's
+    component."""
+    rng = np.random.default_rng(seed)
+    rows, cols, off = [], [], 0
+    for m in sizes:
+        a = np.arange(m)
+        rows += list(off + a)
+        cols += list(off + (a + 1) % m)
+        ch = rng.integers(0, m, (m, 2))
+        ch = ch[ch[:, 0] != ch[:, 1]]
+        rows += list(off + ch[:, 0])
+        cols += list(off + ch[:, 1])
+        off += m
+    r, c = np.array(rows), np.array(cols)
+    e = np.unique(np.stack([np.minimum(r, c), np.maximum(r, c)], 1), axis=0)
+    g = wl.csr_from_undirected(off, e[:, 0], e[:, 1], rng.uniform(0.5, 1.5, len(e)), np.float64)
+    return g, np.repeat(np.arange(len(sizes)), sizes)
+
+
+def sin_largest_angle(U, V):
+    """sin of the largest principal angle between span(U) and span(V)."""
+    Qu, Qv = oracle.qf(U), oracle.qf(V)
+    return np.linalg.norm(Qu - Qv @ (Qv.T @ Qu), 2)
+
+
+@pytest.mark.parametrize("p,f_ratio,angle", [(1.5, 1e-3, 0.02), (1.2, 0.05, 0.15)])
+def test_p_below_2_stage_approaches_the_component_span(p, f_ratio, angle):
+    g, comp = components_graph([30, 24, 36], 3)
+    k = 3
+    ind = np.zeros((g.n, k))
+    ind[np.arange(g.n), comp] = 1.0
+    U0 = oracle.qf(ind + 0.2 * np.random.default_rng(5).standard_normal(ind.shape))
+    assert sin_largest_angle(U0, ind) > 0.3
+    U, st = oracle.rtr_newton(g, U0, p, oracle.SolveOptions(max_outer=100, gtol_rel=1e-9))
+    F0, F = oracle.objective(g, U0, p), oracle.objective(g, U, p)
+    assert 0.0 <= F <= f_ratio * F0, (F, F0)
+    assert sin_largest_angle(U, ind) <= angle
+    labels = oracle.kmeans(U, k)[0]
+    assert len(set(zip(comp.tolist(), labels.tolist()))) == k  # the components, up to a permutation
+
+
+@pytest.mark.parametrize("p", [1.5, 1.2])
+def test_p_below_2_stage_stops_on_the_optimum(p):
+    """Started on the component span, every difference inside a component is
+    a tie: the gradient is exactly zero and the stage takes no step."""
+    g, comp = components_graph([30, 24, 36], 3)
+    ind = np.zeros((g.n, 3))
+    ind[np.arange(g.n), comp] = 1.0
+    U, st = oracle.rtr_newton(g, oracle.qf(ind), p, oracle.SolveOptions())
+    assert st["outer"] == 0 and st["gnorm"] == 0.0 and oracle.objective(g, U, p) == 0.0
+
+
+def test_p_below_2_solve_ends_with_zero_rcut_on_components():
+    """The whole solve below p = 2 (two stages, k-means, RCut) from a
+    perturbed indicator block: the components, and RCut = 0 (no edge cut)."""
+    g, comp = components_graph([30, 24, 36], 3)
+    k = 3
+    ind = np.zeros((g.n, k))
+    ind[np.arange(g.n), comp] = 1.0
+    U0 = oracle.qf(ind + 0.2 * np.random.default_rng(7).standard_normal(ind.shape))
+    U, labels, rc, stages = oracle.solve(g, U0, (1.6, 1.3), oracle.SolveOptions(max_outer=60))
+    assert rc == 0.0
+    assert len(set(zip(comp.tolist(), labels.tolist()))) == k
+    assert stages[0]["f"] <= 1e-12 * oracle.objective(g, U0, 1.6)
+
+
+def test_p_below_2_newton_converges_quadratically():
+    """Near a minimiser where no difference vanishes, F_p is smooth and
+    Riemannian Newton with the exact Hessian converges quadratically (Absil,
+    Mahony & Sepulchre, Thm. 7.4.11; truncated CG stops at ||r|| <=
+    ||g||^(1 + theta), theta = 1): once ||grad|| is below 1e-6 of its start
+    it reaches 1e-12 within three steps.  Algorithm 1's form, which leaves out
+    the quotient's rank-two terms, is not the Hessian of F_p, and from the same
+    start it converges only linearly (not below 1e-8 in 80 steps)."""
+    g = wl.sbm_sampled(np.random.default_rng(3), 150, 3, 8.0, 0.85, np.float64)
+    k = 3
+    U2, _ = oracle.rtr_newton(g, wl.orthonormal_block(3, g.n, k, np.float64), 2.0,
+                              oracle.SolveOptions(max_outer=60, gtol_rel=1e-12))
+    U, st = oracle.rtr_newton(g, U2, 1.5, oracle.SolveOptions(max_outer=80, gtol_rel=1e-12))
+    h = np.array(st["history"]) / st["gnorm0"]
+    assert h[-1] <= 1e-12
+    first = int(np.argmax(h <= 1e-6))
+    assert h[first] <= 1e-6 and len(h) - 1 - first <= 3, h[-8:]
+    _, sta = oracle.rtr_newton(g, U2, 1.5, oracle.SolveOptions(max_outer=80, gtol_rel=1e-12, hessian="alg1"))
+    assert min(sta["history"]) / sta["gnorm0"] > 1e-8
