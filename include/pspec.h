@@ -375,7 +375,9 @@ pspec_status pspec_solve_batched(pspec_graph* g, int k, const double* p_schedule
  *               of such a graph are left as they were)
  *   stats_out   host pspec_solve_stats[G] or NULL: each graph's counters
  *               (seconds = the whole call's wall time)
- * The FP32 path; opts->verbose prints one line per Newton step of the batch.
+ * The FP32 path; opts->verbose = 1 prints one line per Newton step of the
+ * batch, 2 also one line per graph that took the step (its F, ||grad||, CG
+ * iterations and stop reason, ratio, radius and decision, as pspec_solve).
  * Synchronises the solve's own stream; joined to `stream` by events.
  * Returns OK, NOT_CONVERGED when a graph's stage hit max_outer, or the first
  * graph error in graph order (INVALID_ARG for a graph with fewer vertices

@@ -54,6 +54,8 @@ struct LsState {
   double rr, norm_r0, stop, e_Pe, e_Pd, d_Pd, alpha, step, beta, d_Hd;
   // trust region
   double f, gnorm, gnorm0, Delta;
+  double rho;  // the last decision's ratio, and its CG count, stop reason and
+  int last_j, last_reason, stepped;  // whether the graph took that step (the verbose trace)
   int j, done, reason, boundary;  // CG iterations, stopped, why (1..4), on the boundary
   int active;                     // still iterating in the current stage
   int converged;                  // the current stage converged
@@ -852,9 +854,13 @@ __global__ void ls_decide_kernel(LsState* st, double* sc, LsOff off, LsOpts o, i
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < G; b += gridDim.x * blockDim.x) {
     LsState& s = st[b];
     s.accept = 0;
+    s.stepped = 0;
     if (skip_newton[b]) continue;  // took no step
     double* x = sc + (size_t)b * off.stride;
     s.inner += s.j;
+    s.stepped = 1;
+    s.last_j = s.j;
+    s.last_reason = s.reason;
     const bool on_boundary = s.boundary != 0;
     const double f_new = x[off.Fn];
     const bool trial_bad = s.status != 0 || !isfinite(f_new);
@@ -864,6 +870,7 @@ __global__ void ls_decide_kernel(LsState* st, double* sc, LsOff off, LsOpts o, i
     const double den = -(x[off.dots] + 0.5 * x[off.dots + 1]) + reg;
     const bool model_decreased = den >= 0.0 && !trial_bad;
     const double rho = trial_bad ? NAN : (den != 0.0 ? num / den : -INFINITY);
+    s.rho = rho;
     if (!model_decreased || rho < 0.25 || isnan(rho))
       s.Delta *= 0.25;
     else if (rho > 0.75 && on_boundary)
@@ -1212,6 +1219,16 @@ pspec_status run_stages(Lockstep& S, const double* sched, int n_p, int verbose) 
                                                                 S.k, S.T, w.st);
       PSPEC_CUDA(cudaGetLastError());
       const int before = active;
+      if (verbose >= 2) {  // each graph that took this step: its decision, before the next step opens
+        std::vector<LsState> hs(G);
+        PSPEC_CUDA(cudaMemcpyAsync(hs.data(), w.st, sizeof(LsState) * G, cudaMemcpyDeviceToHost, S.s));
+        PSPEC_CUDA(cudaStreamSynchronize(S.s));
+        for (int b = 0; b < G; ++b)
+          if (hs[b].stepped)
+            std::fprintf(stderr, "pspec lockstep graph=%d p=%.3f step=%d f=%.10e |g|=%.3e tcg=%d(%d) rho=%.3f Delta=%.3e %s\n",
+                         b, p, step, hs[b].f, hs[b].gnorm, hs[b].last_j, hs[b].last_reason, hs[b].rho, hs[b].Delta,
+                         hs[b].accept ? "acc" : "rej");
+      }
       PSPEC_TRY(S.count_open(w.skip_newton, &active));
       if (verbose)
         std::fprintf(stderr, "pspec lockstep p=%.3f step=%d graphs=%d tcg_chunks=%d still=%d\n", p, step, before,
