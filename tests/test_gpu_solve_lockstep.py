@@ -269,3 +269,25 @@ def test_lockstep_with_hub_rows(api):
         assert abs(stats[i]["f"][0] - ev) <= 1e-5 * ev, (i, stats[i]["f"][0], ev)
         assert abs(stats[i]["f"][0] - sti["f"][0]) <= 1e-5 * ev, (i, stats[i]["f"][0], sti["f"][0])
         assert abs(rc[i] - rci) <= 0.02 * rci, (i, rc[i], rci)
+
+
+def test_lockstep_nan_start_stops_only_its_graph(api):
+    """A NaN in one graph's starting block is reported for that graph
+    (NONFINITE, RCut NaN) at its first evaluation; the other graphs' solves are
+    those they have alone."""
+    rng = np.random.default_rng(19)
+    gs = [wl.sbm_sampled(rng, 500, 3, 9.0, 0.9), wl.sbm_sampled(rng, 700, 3, 9.0, 0.9),
+          wl.sbm_sampled(rng, 300, 3, 9.0, 0.9)]
+    batch = wl.concat_graphs(gs, [3] * len(gs))
+    G = handle(api, batch)
+    U = np.concatenate([wl.orthonormal_block(30 + i, g.n, 3) for i, g in enumerate(gs)])
+    U[batch.node_off[1] + 17, 2] = np.nan
+    _, _, rc, status, stats, st = G.solve_lockstep(torch.from_numpy(U).cuda(), [2.0, 1.7], allow_errors=True)
+    assert status[1] == api._abi.PSPEC_ERR_NONFINITE and math.isnan(rc[1])
+    assert st == api._abi.PSPEC_ERR_NONFINITE
+    for i in (0, 2):
+        a, b = batch.node_off[i], batch.node_off[i + 1]
+        _, _, rci, sti, _ = api.Graph.from_csr(gs[i]).solve(torch.from_numpy(U[a:b]).cuda(), [2.0, 1.7])
+        assert status[i] in (0, 6)
+        assert abs(stats[i]["f"][0] - sti["f"][0]) <= 1e-5 * sti["f"][0]
+        assert abs(rc[i] - rci) <= 0.01 * rci
