@@ -42,11 +42,6 @@
 
 namespace pspec {
 
-// Entries per lane per row before a row gets more edge slots, by default: 8,
-// so a task holds at most 256 / Q entries (a hub chunk is that long), which
-// fits the staged kernel's buffers for k = 4, 8 and 16 (edge_staged.cuh).
-__host__ __device__ constexpr int edges_per_lane(int /*Q*/) { return 8; }
-
 struct EdgeArgs {
   const int2* cw;         // degree-sorted entries: x = column, y = bits of log2 w
   const int32_t* perm;    // sorted row -> vertex

@@ -5,9 +5,9 @@
 // used whenever a task's entries fit its shared-memory buffers (entries per
 // task 32 L / Q <= staged_max_entries(K)), and the direct kernel
 // (edge_kernels.cuh) for longer tasks and for batch launches that leave
-// graphs out (graph_skip).  The edges-per-lane target L of the
-// handle's task set -- set by pspec_tune or PSPEC_EDGES_PER_LANE -- thus also
-// picks the kernel.
+// graphs out (graph_skip).  The edges-per-lane target L of the handle's task
+// set -- set by pspec_tune or PSPEC_EDGES_PER_LANE, 16 Q by default (direct) --
+// thus also picks the kernel.
 #pragma once
 
 #include <algorithm>

@@ -149,10 +149,15 @@ pspec_status ensure_tasks(pspec_graph* g, int Q) {
   int qi = Q == 1 ? 0 : Q == 2 ? 1 : 2;
   TaskSet& ts = g->tasks[qi];
   if (ts.built) return PSPEC_OK;
-  // at most edges_per_lane(Q) entries per lane and row before the row gets
-  // more edge slots; hub chunks give each lane that many entries
+  // at most L entries per lane and row before the row gets more edge slots;
+  // hub chunks give each lane that many entries.  L is the handle's (set by
+  // pspec_tune), else PSPEC_EDGES_PER_LANE, else 16 Q: the largest of the
+  // tuner's candidates, which it chose (or came within 4 % of) on the grid,
+  // kNN, degree-corrected SBM and batch workloads.  Its tasks (32 L / Q
+  // entries) are too long for the staged kernel, so the direct kernel runs;
+  // 8 entries per lane would pick the staged kernel, 1.3x to 1.9x slower there.
   const int L = std::max(1, g->edges_per_lane[qi] > 0 ? g->edges_per_lane[qi]
-                                                      : env_int("PSPEC_EDGES_PER_LANE", edges_per_lane(Q)));
+                                                      : env_int("PSPEC_EDGES_PER_LANE", 16 * Q));
   const int max_slots = 32 / Q;
   int max_elog = 0;
   while ((1 << max_elog) < max_slots) ++max_elog;

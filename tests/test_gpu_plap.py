@@ -230,3 +230,29 @@ def test_invalid_arguments(api, graphs):
     buf = torch.zeros(g.n * 4 + 1, device="cuda")
     with pytest.raises(_abi.PspecError):
         G.eval(buf[1:].view(g.n, 4), 1.5)
+
+
+@pytest.mark.parametrize("k", [4, 8, 16])
+def test_staged_kernel_parity(api, k, monkeypatch):
+    """The staged (cp.async) edge kernel, which runs when a task's entries fit
+    its buffers (here 8 entries per lane, set through PSPEC_EDGES_PER_LANE;
+    the default shape runs the direct kernel): F, gradient, the Hessian
+    product and the kept-point Hessian product against the oracle, on a graph
+    with hub rows and on one with heavy weights and exact ties."""
+    from gpu_common import TOL_HVP, star_plus_powerlaw
+    monkeypatch.setenv("PSPEC_EDGES_PER_LANE", "8")
+    cases = [(star_plus_powerlaw(seed=11, n=4000), lambda n: wl.orthonormal_block(41, n, k)),
+             (tied_heavy_graph(3, 2000), lambda n: quantised_block(43, n, k))]
+    for g, make_u in cases:
+        G = api.Graph.from_csr(g)
+        U = make_u(g.n)
+        V = wl.gaussian_block(42, g.n, k)
+        for p in (1.3, 2.0):
+            check_eval(api, g, G, U, p)
+            check_hvp(api, g, G, U, V, p)
+            Ud, Vd = torch.from_numpy(U).cuda(), torch.from_numpy(V).cuda()
+            G.eval(Ud, p, keep_delta=True)
+            HVk = G.hvp(Ud, Vd, p, delta_kept=True)
+            torch.cuda.synchronize()
+            ref = oracle.euclidean_hvp(g, U.astype(np.float64), V.astype(np.float64), p)
+            assert rel_col(HVk.cpu().numpy(), ref) <= TOL_HVP
