@@ -67,6 +67,8 @@ def parse():
                     help="full solve to the schedule's last p: FP32 only, or FP32 and plain FP64")
     ap.add_argument("--solve-gtol", type=float, default=None,
                     help="relative gradient tolerance of every stage (library default 1e-6)")
+    ap.add_argument("--solve-max-outer", type=int, default=None,
+                    help="Newton steps allowed per stage (library default 30)")
     ap.add_argument("--no-solve", action="store_true", help="same as --solve none")
     ap.add_argument("--solve-perturbed", action="store_true",
                     help="with --solve both: also the FP64 solve from U0 perturbed at FP32 rounding")
@@ -601,7 +603,12 @@ def main():
     if args.solve != "none" and rank == 0 and len(parts) == 1:
         pt = parts[0]
         sched = list(info["p_schedule"])
-        opts = api.default_opts() if args.solve_gtol is None else api.default_opts(gtol_rel=args.solve_gtol)
+        kw = {}
+        if args.solve_gtol is not None:
+            kw["gtol_rel"] = args.solve_gtol
+        if args.solve_max_outer is not None:
+            kw["max_outer"] = args.solve_max_outer
+        opts = api.default_opts(**kw)
         cap = opts.max_outer
 
         def run_solve(U0):
