@@ -35,7 +35,8 @@ namespace {
 
 template <typename T>
 struct SolveWork {
-  T *U, *Unew, *egrad, *egrad_new, *rg, *rg_new, *eta, *Heta, *r, *delta, *He, *Hd, *tmp;
+  // (H eta is not kept: it is r - rg when truncated CG stops)
+  T *U, *Unew, *egrad, *egrad_new, *rg, *rg_new, *eta, *r, *delta, *He, *Hd, *tmp;
   // Delta_p u and N, D of the iterate and of the trial point (FP32: the
   // Hessian products of truncated CG reuse the iterate's; they swap with it)
   T *dk, *dk_new;
@@ -62,7 +63,7 @@ pspec_status carve(pspec_graph* g, int k, SolveWork<T>* w) {
   const int groups = (maxb + kGroup - 1) / kGroup;
   const size_t red = sizeof(double) * 256 * (size_t)(maxb + groups);
   const size_t small = 4096 * sizeof(double);
-  const size_t need = 15 * vec + 2 * red + small;
+  const size_t need = 14 * vec + 2 * red + small;
   if (g->d_solve_bytes < need) {
     if (g->d_solve) cudaFree(g->d_solve);
     g->d_solve = nullptr;
@@ -71,8 +72,8 @@ pspec_status carve(pspec_graph* g, int k, SolveWork<T>* w) {
     g->d_solve_bytes = need;
   }
   char* p = (char*)g->d_solve;
-  T** vecs[15] = {&w->U, &w->Unew, &w->egrad, &w->egrad_new, &w->rg, &w->rg_new, &w->eta,
-                  &w->Heta, &w->r, &w->delta, &w->He, &w->Hd, &w->tmp, &w->dk, &w->dk_new};
+  T** vecs[14] = {&w->U, &w->Unew, &w->egrad, &w->egrad_new, &w->rg, &w->rg_new, &w->eta,
+                  &w->r, &w->delta, &w->He, &w->Hd, &w->tmp, &w->dk, &w->dk_new};
   for (auto v : vecs) {
     *v = (T*)p;
     p += vec;
@@ -334,7 +335,6 @@ static pspec_status solve_impl(pspec_graph* g, int k, const double* sched, int n
       h.max_inner = o.max_inner;
       PSPEC_CUDA(cudaMemcpyAsync(w.st, &h, sizeof(TcgState), cudaMemcpyHostToDevice, s));
       PSPEC_CUDA(cudaMemsetAsync(w.eta, 0, sizeof(T) * m, s));
-      PSPEC_CUDA(cudaMemsetAsync(w.Heta, 0, sizeof(T) * m, s));
       PSPEC_CUDA(cudaMemcpyAsync(w.r, w.rg, sizeof(T) * m, cudaMemcpyDeviceToDevice, s));
       PSPEC_TRY(S.combine(w.delta, w.rg, -1.0, nullptr, 0.0, nullptr, nullptr, nullptr, nullptr));
       const int* done = &w.st->done;
@@ -345,7 +345,7 @@ static pspec_status solve_impl(pspec_graph* g, int k, const double* sched, int n
           PSPEC_TRY(S.hvp_gram(w.U, w.delta, p, w.He, w.G, done));
           TimedScope timer(g, "solve_tcg_vec", s);
           S.hess(w.st);
-          cg_update_kernel<T><<<w.vblocks, kSolveBlock, 0, s>>>(w.eta, w.Heta, w.r, w.delta,
+          cg_update_kernel<T><<<w.vblocks, kSolveBlock, 0, s>>>(w.eta, w.r, w.delta,
                                                                  w.Hd, m, w.st, w.gr);
           direction_kernel<T><<<w.vblocks, kSolveBlock, 0, s>>>(w.delta, w.r, m, w.st);
           PSPEC_CUDA(cudaGetLastError());
@@ -380,13 +380,13 @@ static pspec_status solve_impl(pspec_graph* g, int k, const double* sched, int n
       dp.x[0] = w.rg;
       dp.y[0] = w.eta;
       dp.x[1] = w.eta;
-      dp.y[1] = w.Heta;
+      dp.y[1] = w.r;  // <eta, H eta> = <eta, r> - <eta, rg>
       dp.np = 2;
       PSPEC_TRY(S.dots(dp, w.dots));
       // the Riemannian gradient at the trial point, used if it is accepted
       PSPEC_TRY(S.riemannian_grad(w.Unew, w.egrad_new, w.Mnew, w.rg_new, w.gdot));
       PSPEC_TRY(S.fetch(true));
-      const double dv[2] = {S.rec->dots[0], S.rec->dots[1]};
+      const double dv[2] = {S.rec->dots[0], S.rec->dots[1] - S.rec->dots[0]};  // <rg, eta>, <eta, H eta>
       const double f_new = S.rec->F;
       // a trial point whose evaluation met a NaN/Inf or a zero column is rejected
       const bool trial_bad = S.rec->status != 0 || !std::isfinite(f_new);

@@ -708,18 +708,17 @@ __global__ void __launch_bounds__(kSolveBlock) hess_kernel(T* Hd, const T* He, c
   }
 }
 
-// eta += step delta; Heta += step Hd; unless on the boundary r += alpha Hd
-// and the partial <r, r>; the last block checks the residual, takes beta.
+// eta += step delta and r += step Hd, with the partial <r, r> unless the step
+// ended on the boundary; the last block checks the residual, takes beta.
+// H eta is not kept: r starts at the Riemannian gradient rg and takes every
+// step's Hd (the boundary step's too), so H eta = r - rg when CG stops.
 template <typename T>
-__global__ void __launch_bounds__(kSolveBlock) cg_update_kernel(T* eta, T* Heta, T* r,
-                                                                const T* delta, const T* Hd,
-                                                                int64_t m, TcgState* st,
-                                                                GridRed gr) {
+__global__ void __launch_bounds__(kSolveBlock) cg_update_kernel(T* eta, T* r, const T* delta, const T* Hd,
+                                                                int64_t m, TcgState* st, GridRed gr) {
   using R = typename RedT<T>::type;
   if (st->done) return;
   __shared__ R s_blk[1], s_tot[1];
   const T step = (T)st->step;
-  const T alpha = (T)st->alpha;
   const bool bnd = st->boundary != 0;
   using V = Vec16<T>;
   using VT = typename V::type;
@@ -733,34 +732,22 @@ __global__ void __launch_bounds__(kSolveBlock) cg_update_kernel(T* eta, T* Heta,
     const VT h = reinterpret_cast<const VT*>(Hd)[e];
     const VT d = reinterpret_cast<const VT*>(delta)[e];
     VT et = reinterpret_cast<VT*>(eta)[e];
-    VT he = reinterpret_cast<VT*>(Heta)[e];
+    VT rr = reinterpret_cast<VT*>(r)[e];
 #pragma unroll
     for (int w = 0; w < W; ++w) {
       V::set(et, w, V::get(et, w) + step * V::get(d, w));
-      V::set(he, w, V::get(he, w) + step * V::get(h, w));
+      const T rn = V::get(rr, w) + step * V::get(h, w);
+      V::set(rr, w, rn);
+      if (!bnd) acc.add(rn * rn);
     }
     reinterpret_cast<VT*>(eta)[e] = et;
-    reinterpret_cast<VT*>(Heta)[e] = he;
-    if (!bnd) {
-      VT rr = reinterpret_cast<VT*>(r)[e];
-#pragma unroll
-      for (int w = 0; w < W; ++w) {
-        const T rn = V::get(rr, w) + alpha * V::get(h, w);
-        V::set(rr, w, rn);
-        acc.add(rn * rn);
-      }
-      reinterpret_cast<VT*>(r)[e] = rr;
-    }
+    reinterpret_cast<VT*>(r)[e] = rr;
   }
   for (int64_t e = mv * W + tid; e < m; e += nth) {
-    const T h = Hd[e];
     eta[e] += step * delta[e];
-    Heta[e] += step * h;
-    if (!bnd) {
-      const T rn = r[e] + alpha * h;
-      r[e] = rn;
-      acc.add(rn * rn);
-    }
+    const T rn = r[e] + step * Hd[e];
+    r[e] = rn;
+    if (!bnd) acc.add(rn * rn);
   }
   R v1[1] = {acc.get()};
   block_sum<R, 1>(v1, s_blk);

@@ -72,7 +72,7 @@ struct LsState {
 struct LsOff {
   int M, Mn, Gm, Gram, Rinv;  // U^T egrad (iterate, trial), U^T H delta, Gram, R^-1
   int nd, ndn;                // N[16], D[16] of the iterate and of the trial point
-  int F, Fn, gd, gdn, dots;   // F, F trial, <rg,rg>, <rg_new,rg_new>, <rg,eta>, <eta,Heta>
+  int F, Fn, gd, gdn, dots;   // F, F trial, <rg,rg>, <rg_new,rg_new>, <rg,eta>, <eta,r>
   int stride;
 };
 
@@ -566,12 +566,13 @@ __global__ void __launch_bounds__(kLsTile) ls_hess_kernel(float* Hd, const float
   }
 }
 
-// eta += step delta, Heta += step Hd, and unless the step ended on the
-// boundary r += alpha Hd with the tile's <r, r>.  The graph's last tile ends
+// eta += step delta and r += step Hd, with the tile's <r, r> unless the step
+// ended on the boundary (H eta is not kept: r starts at rg and takes every
+// step's Hd, so H eta = r - rg when CG stops).  The graph's last tile ends
 // the CG iteration: stop on the boundary, at the residual threshold or at
 // max_inner (the graph is then flagged in skip); otherwise beta and the
 // recurrences for <eta, delta> and <delta, delta>.
-__global__ void __launch_bounds__(kLsTile) ls_cg_update_kernel(float* eta, float* Heta, float* r,
+__global__ void __launch_bounds__(kLsTile) ls_cg_update_kernel(float* eta, float* r,
                                                                const float* __restrict__ delta,
                                                                const float* __restrict__ Hd, int k, LsTiles T,
                                                                int* skip, LsState* st, int max_inner) {
@@ -581,7 +582,6 @@ __global__ void __launch_bounds__(kLsTile) ls_cg_update_kernel(float* eta, float
     const int b = td.x;
     if (skip[b]) continue;
     const float step = (float)st[b].step;
-    const float alpha = (float)st[b].alpha;
     const bool bnd = st[b].boundary != 0;
     const int64_t e0 = (int64_t)td.y * k;
     const int cnt = td.z * k;
@@ -589,14 +589,10 @@ __global__ void __launch_bounds__(kLsTile) ls_cg_update_kernel(float* eta, float
     acc.init();
     for (int e = threadIdx.x; e < cnt; e += kLsTile) {
       const int64_t i = e0 + e;
-      const float h = Hd[i];
       eta[i] += step * delta[i];
-      Heta[i] += step * h;
-      if (!bnd) {
-        const float rn = r[i] + alpha * h;
-        r[i] = rn;
-        acc.add(rn * rn);
-      }
+      const float rn = r[i] + step * Hd[i];
+      r[i] = rn;
+      if (!bnd) acc.add(rn * rn);
     }
     float2 v1[1] = {kahan_to_ff(acc)};
     ls_block_sum<1>(v1, s_out);
@@ -645,8 +641,8 @@ __global__ void __launch_bounds__(kLsTile) ls_direction_kernel(float* delta, con
   }
 }
 
-// truncated CG's start: eta = 0, Heta = 0, r = rg, delta = -rg
-__global__ void __launch_bounds__(kLsTile) ls_tcg_init_kernel(float* eta, float* Heta, float* r, float* delta,
+// truncated CG's start: eta = 0, r = rg, delta = -rg
+__global__ void __launch_bounds__(kLsTile) ls_tcg_init_kernel(float* eta, float* r, float* delta,
                                                               const float* __restrict__ rg, int k, LsTiles T,
                                                               const int* skip) {
   for (int tile = blockIdx.x; tile < T.n; tile += gridDim.x) {
@@ -657,7 +653,6 @@ __global__ void __launch_bounds__(kLsTile) ls_tcg_init_kernel(float* eta, float*
     for (int e = threadIdx.x; e < cnt; e += kLsTile) {
       const float g = rg[e0 + e];
       eta[e0 + e] = 0.f;
-      Heta[e0 + e] = 0.f;
       r[e0 + e] = g;
       delta[e0 + e] = -g;
     }
@@ -677,11 +672,12 @@ __global__ void __launch_bounds__(kLsTile) ls_add_kernel(float* out, const float
   }
 }
 
-// the tile's <rg, eta> and <eta, Heta> (the model's decrease); the graph's
+// the tile's <rg, eta> and <eta, r> (the model's decrease, <eta, H eta> =
+// <eta, r> - <eta, rg>); the graph's
 // last tile writes both
 __global__ void __launch_bounds__(kLsTile) ls_dots2_kernel(const float* __restrict__ rg,
                                                            const float* __restrict__ eta,
-                                                           const float* __restrict__ Heta, int k, LsTiles T,
+                                                           const float* __restrict__ r, int k, LsTiles T,
                                                            const int* skip, double* sc, int stride, int dots_off) {
   __shared__ double s_out[2];
   for (int tile = blockIdx.x; tile < T.n; tile += gridDim.x) {
@@ -696,7 +692,7 @@ __global__ void __launch_bounds__(kLsTile) ls_dots2_kernel(const float* __restri
     for (int e = threadIdx.x; e < cnt; e += kLsTile) {
       const float x = eta[e0 + e];
       a0.add(rg[e0 + e] * x);
-      a1.add(x * Heta[e0 + e]);
+      a1.add(x * r[e0 + e]);
     }
     float2 v2[2] = {kahan_to_ff(a0), kahan_to_ff(a1)};
     ls_block_sum<2>(v2, s_out);
@@ -867,7 +863,7 @@ __global__ void ls_decide_kernel(LsState* st, double* sc, LsOff off, LsOpts o, i
     s.status = 0;
     const double reg = o.rho_reg * fmax(1.0, fabs(s.f));
     const double num = s.f - f_new + reg;
-    const double den = -(x[off.dots] + 0.5 * x[off.dots + 1]) + reg;
+    const double den = -(x[off.dots] + 0.5 * (x[off.dots + 1] - x[off.dots])) + reg;  // <rg,eta> + <eta,H eta>/2
     const bool model_decreased = den >= 0.0 && !trial_bad;
     const double rho = trial_bad ? NAN : (den != 0.0 ? num / den : -INFINITY);
     s.rho = rho;
@@ -959,7 +955,7 @@ __global__ void __launch_bounds__(256) ls_rcut_kernel(const double* __restrict__
 // ------------------------------------------------------------------ host ---
 struct LsWork {
   std::vector<void*> allocs;
-  float *U = nullptr, *Un, *eg, *egn, *rg, *rgn, *dk, *dkn, *eta, *Heta, *r, *delta, *He, *Hd, *tmp;
+  float *U = nullptr, *Un, *eg, *egn, *rg, *rgn, *dk, *dkn, *eta, *r, *delta, *He, *Hd, *tmp;
   int4* tiles = nullptr;
   int32_t* graph_tile = nullptr;
   int n_tiles = 0;
@@ -1047,7 +1043,7 @@ struct Lockstep {
     }
     {
       TimedScope timer(g, "ls_cg_update", s);
-      ls_cg_update_kernel<<<rows_blocks, kLsTile, 0, s>>>(w.eta, w.Heta, w.r, w.delta, w.Hd, k, T, w.skip_cg,
+      ls_cg_update_kernel<<<rows_blocks, kLsTile, 0, s>>>(w.eta, w.r, w.delta, w.Hd, k, T, w.skip_cg,
                                                           w.st, o.max_inner);
     }
     {
@@ -1096,8 +1092,8 @@ pspec_status setup(Lockstep& S, const std::vector<int64_t>& off, int k) {
   const int G = S.G;
   LsWork& w = S.w;
   const size_t m = (size_t)g->n * k;
-  float** vecs[15] = {&w.U, &w.Un, &w.eg, &w.egn, &w.rg, &w.rgn, &w.dk, &w.dkn,
-                      &w.eta, &w.Heta, &w.r, &w.delta, &w.He, &w.Hd, &w.tmp};
+  float** vecs[14] = {&w.U, &w.Un, &w.eg, &w.egn, &w.rg, &w.rgn, &w.dk, &w.dkn,
+                      &w.eta, &w.r, &w.delta, &w.He, &w.Hd, &w.tmp};
   for (float** v : vecs) PSPEC_TRY(w.alloc(v, m));
   std::vector<int4> tiles;
   std::vector<int32_t> graph_tile(G + 1, 0);
@@ -1177,7 +1173,7 @@ pspec_status run_stages(Lockstep& S, const double* sched, int n_p, int verbose) 
     int step = 0;
     while (active > 0) {
       ++step;
-      ls_tcg_init_kernel<<<S.rows_blocks, kLsTile, 0, S.s>>>(w.eta, w.Heta, w.r, w.delta, w.rg, S.k, S.T,
+      ls_tcg_init_kernel<<<S.rows_blocks, kLsTile, 0, S.s>>>(w.eta, w.r, w.delta, w.rg, S.k, S.T,
                                                               w.skip_cg);
       PSPEC_CUDA(cudaGetLastError());
       int chunks = 0;
@@ -1212,7 +1208,7 @@ pspec_status run_stages(Lockstep& S, const double* sched, int n_p, int verbose) 
       }
       PSPEC_TRY(S.trial_point());
       PSPEC_TRY(S.eval(w.Un, p, w.dkn, w.egn, w.rgn, w.off.ndn, w.off.Fn, w.off.Mn, w.off.gdn));
-      ls_dots2_kernel<<<S.rows_blocks, kLsTile, 0, S.s>>>(w.rg, w.eta, w.Heta, S.k, S.T, w.skip_newton, w.sc,
+      ls_dots2_kernel<<<S.rows_blocks, kLsTile, 0, S.s>>>(w.rg, w.eta, w.r, S.k, S.T, w.skip_newton, w.sc,
                                                            w.off.stride, w.off.dots);
       ls_decide_kernel<<<1, 256, 0, S.s>>>(w.st, w.sc, w.off, S.o, S.kk, w.skip_newton, w.skip_cg, G);
       ls_accept_rows_kernel<<<S.rows_blocks, kLsTile, 0, S.s>>>(w.U, w.Un, w.eg, w.egn, w.dk, w.dkn, w.rg, w.rgn,
